@@ -1,0 +1,238 @@
+"""Seeded synthetic inputs shared by the oracle tests, the CUDA parity tests and the bench.
+
+This module holds only input preparation: material constants, the five workload
+configurations, seeded density designs and Bloch wavevector paths.  It contains
+none of the band-structure or sensitivity arithmetic, and it imports neither the
+oracle nor the CUDA binding.
+
+Workload recipe (the paper's optimized designs exist only as figures, so seeded
+designs with the same shapes stand in for them):
+
+* two-phase tungsten-carbide / epoxy cells on SC, BCC and FCC primitive cells,
+  voxel densities rho_e in [0, 1] with rho_e = 1 the stiff, heavy phase;
+* config 0: SC 8^3 binary cube inclusion, M = 1, 10 k on G-X-M-G-R, 6 bands;
+* config 1: SC 16^3 periodic Gaussian random field through a sigmoid, p = 3,
+  M = 2, 30 k on the irreducible-zone boundary, 12 bands;
+* config 2: BCC 24^3 random field in fractional coordinates, M = 3, 64 k, 16 bands;
+* config 3: FCC 32^3 smoothed level set of an 8-term trigonometric sum,
+  M = 4 (729 plane waves), 100 k, 20 bands;
+* config 4: 32 designs of mixed lattice, cutoff and grid, 48 k, 20 bands.
+
+Seeds: numpy.random.default_rng(1603 + 1000 * config + design_index).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Material constants (SI).  phase1 is rho_e = 1, phase0 is rho_e = 0.
+TUNGSTEN_CARBIDE = dict(rho=15800.0, E=600e9, nu=0.22)
+EPOXY = dict(rho=1180.0, E=4.35e9, nu=0.37)
+# The constants the paper quotes for its sphere scans (Results, normalized band gaps).
+PAPER_WC = dict(rho=13800.0, E=387.5559e9, nu=0.3459)
+PAPER_EPOXY = dict(rho=1180.0, E=4.3438e9, nu=0.3679)
+
+
+# Primitive vectors (columns, units of the cubic lattice constant).  A private
+# copy used only to express high-symmetry points in reduced coordinates.
+def _primitive(lattice: str) -> np.ndarray:
+    if lattice == "sc":
+        return np.eye(3)
+    if lattice == "bcc":
+        return 0.5 * np.array([[-1.0, 1.0, 1.0], [1.0, -1.0, 1.0], [1.0, 1.0, -1.0]]).T
+    if lattice == "fcc":
+        return 0.5 * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]]).T
+    raise ValueError(lattice)
+
+
+# High-symmetry points, Cartesian, units of 1/a (no 2*pi).
+HIGH_SYMMETRY = {
+    "sc": {"G": (0, 0, 0), "X": (0, 0.5, 0), "M": (0.5, 0.5, 0), "R": (0.5, 0.5, 0.5)},
+    "bcc": {"G": (0, 0, 0), "H": (0, 0, 1), "N": (0.5, 0.5, 0), "P": (0.5, 0.5, 0.5)},
+    "fcc": {"G": (0, 0, 0), "X": (0, 1, 0), "W": (0.5, 1, 0), "K": (0.75, 0.75, 0),
+            "L": (0.5, 0.5, 0.5), "U": (0.25, 1, 0.25)},
+}
+# Boundary paths of the irreducible zones; '|' is a jump.
+PATHS = {
+    "sc": "G-X-M-G-R-X|M-R",
+    "sc_short": "G-X-M-G-R",
+    "bcc": "G-H-N-G-P-H|P-N",
+    "fcc": "G-X-W-K-G-L-U-W-L-K|U-X",
+}
+
+
+def kpath(lattice: str, nk: int, path: str | None = None) -> np.ndarray:
+    """nk wavevectors on a high-symmetry path, in reduced coordinates Q (nk, 3).
+
+    Every vertex is included; the remaining points are shared between the
+    segments in proportion to their length (largest remainder).  Q_j = K . a_j.
+    """
+    spec = PATHS[path or lattice]
+    pts = HIGH_SYMMETRY[lattice]
+    polylines = [[np.array(pts[s], float) for s in part.split("-")] for part in spec.split("|")]
+    vertices = sum(len(p) for p in polylines)
+    if nk < vertices:
+        raise ValueError(f"need at least {vertices} points for path {spec}")
+    segs = [(pl[i], pl[i + 1]) for pl in polylines for i in range(len(pl) - 1)]
+    lens = np.array([np.linalg.norm(b - a) for a, b in segs])
+    extra = nk - vertices
+    share = extra * lens / lens.sum()
+    alloc = np.floor(share).astype(int)
+    order = np.argsort(-(share - alloc), kind="stable")
+    alloc[order[: extra - alloc.sum()]] += 1
+    out = []
+    si = 0
+    for pl in polylines:
+        out.append(pl[0])
+        for i in range(len(pl) - 1):
+            a, b = pl[i], pl[i + 1]
+            m = alloc[si]
+            for t in range(1, m + 1):
+                out.append(a + (b - a) * t / (m + 1))
+            out.append(b)
+            si += 1
+    K = np.array(out)
+    assert K.shape[0] == nk
+    A = _primitive(lattice)
+    return K @ A  # Q_j = K . a_j
+
+
+def _sigmoid(z):
+    return 1.0 / (1.0 + np.exp(-z))
+
+
+def gaussian_random_field(n: tuple[int, int, int], ell: float, rng, cart: np.ndarray | None = None):
+    """Periodic Gaussian random field: white noise circularly filtered by exp(-|r|^2 / (2 ell^2)),
+    standardised to zero mean and unit variance.  r is the minimum-image offset in fractional
+    coordinates, mapped to Cartesian by ``cart`` when given."""
+    w = rng.standard_normal(n)
+    grids = np.meshgrid(*[np.arange(k) / k for k in n], indexing="ij")
+    d = np.stack([(g + 0.5) % 1.0 - 0.5 for g in grids], axis=-1)
+    if cart is not None:
+        d = d @ cart.T
+    kern = np.exp(-np.sum(d * d, axis=-1) / (2 * ell * ell))
+    z = np.real(np.fft.ifftn(np.fft.fftn(w) * np.fft.fftn(kern)))
+    z = (z - z.mean()) / z.std()
+    return z
+
+
+def trig_levelset_design(n: tuple[int, int, int], rng, terms: int = 8) -> np.ndarray:
+    """Smooth single-network inclusion: phi(s) = sum_j a_j cos(2 pi m_j.s + phi_j),
+    thresholded at its median and smoothed by a sigmoid of slope 8 / std(phi)."""
+    ms = []
+    while len(ms) < terms:
+        m = rng.integers(-2, 3, size=3)
+        if np.any(m != 0):
+            ms.append(m)
+    a = rng.standard_normal(terms)
+    ph = rng.uniform(0.0, 2 * np.pi, size=terms)
+    grids = np.meshgrid(*[(np.arange(k) + 0.5) / k for k in n], indexing="ij")
+    s = np.stack(grids, axis=-1)
+    phi = np.zeros(n)
+    for j in range(terms):
+        phi += a[j] * np.cos(2 * np.pi * (s @ ms[j]) + ph[j])
+    t = np.median(phi)
+    return _sigmoid(8.0 * (phi - t) / phi.std())
+
+
+@dataclasses.dataclass
+class Workload:
+    """One design evaluation: lattice, grid, cutoff, bands, k-points, density."""
+    name: str
+    lattice: str
+    n: tuple[int, int, int]
+    M: int
+    nbands: int
+    Q: np.ndarray            # (nk, 3) reduced wavevectors
+    rho: np.ndarray          # (n0, n1, n2) densities in [0, 1], C order
+    penal: float
+    gaps: tuple[int, ...]    # 1-based lower band of each requested gap
+    seed: int
+    a: float = 1.0
+    phase1: dict = dataclasses.field(default_factory=lambda: dict(TUNGSTEN_CARBIDE))
+    phase0: dict = dataclasses.field(default_factory=lambda: dict(EPOXY))
+
+    @property
+    def N(self) -> int:
+        return (2 * self.M + 1) ** 3
+
+    @property
+    def nk(self) -> int:
+        return self.Q.shape[0]
+
+
+def seed_for(config: int, design: int = 0) -> int:
+    return 1603 + 1000 * config + design
+
+
+def config0() -> Workload:
+    n = (8, 8, 8)
+    rho = np.zeros(n)
+    rho[2:6, 2:6, 2:6] = 1.0
+    return Workload("sc8_M1_binary_cube", "sc", n, 1, 6, kpath("sc", 10, "sc_short"), rho,
+                    1.0, (3,), seed_for(0))
+
+
+def config1(design: int = 0) -> Workload:
+    seed = seed_for(1, design)
+    rng = np.random.default_rng(seed)
+    n = (16, 16, 16)
+    z = gaussian_random_field(n, 1.0 / 6.0, rng, cart=np.eye(3))
+    return Workload("sc16_M2_grf", "sc", n, 2, 12, kpath("sc", 30), _sigmoid(z), 3.0, (3, 6), seed)
+
+
+def config2(design: int = 0) -> Workload:
+    seed = seed_for(2, design)
+    rng = np.random.default_rng(seed)
+    n = (24, 24, 24)
+    z = gaussian_random_field(n, 1.0 / 6.0, rng)
+    return Workload("bcc24_M3_grf", "bcc", n, 3, 16, kpath("bcc", 64), _sigmoid(z), 3.0, (6,), seed)
+
+
+def config3(design: int = 0) -> Workload:
+    seed = seed_for(3, design)
+    rng = np.random.default_rng(seed)
+    n = (32, 32, 32)
+    rho = trig_levelset_design(n, rng)
+    return Workload("fcc32_M4_levelset", "fcc", n, 4, 20, kpath("fcc", 100), rho, 3.0, (6,), seed)
+
+
+def config4() -> list[Workload]:
+    """Uneven batch: 12 SC, 10 BCC, 10 FCC designs; N drawn from {125, 343, 729, 1331}."""
+    out = []
+    lattices = ["sc"] * 12 + ["bcc"] * 10 + ["fcc"] * 10
+    for i, lat in enumerate(lattices):
+        seed = seed_for(4, i)
+        rng = np.random.default_rng(seed)
+        M = int(rng.choice([2, 3, 4, 5]))
+        grid_choices = [g for g in (16, 20, 24, 28, 32, 36, 40) if g >= 2 * M + 1]
+        g = int(rng.choice(grid_choices))
+        n = (g, g, g)
+        cart = np.eye(3) if lat == "sc" else None
+        z = gaussian_random_field(n, 1.0 / 6.0, rng, cart=cart)
+        out.append(Workload(f"{lat}{g}_M{M}_grf_{i}", lat, n, M, 20, kpath(lat, 48), _sigmoid(z),
+                            3.0, (6,), seed))
+    return out
+
+
+CONFIGS = {0: config0, 1: config1, 2: config2, 3: config3}
+
+
+def homogeneous(lattice: str, n, M: int, nbands: int, nk: int, value: float = 0.0) -> Workload:
+    rho = np.full(tuple(n), float(value))
+    return Workload(f"{lattice}_homog", lattice, tuple(n), M, nbands, kpath(lattice, nk), rho, 1.0, (3,), 0)
+
+
+def laminate(n1: int, n_other: int, M: int, frac1: float, kx: list[float]) -> Workload:
+    """SC cell layered along x: rho = 1 on the first round(frac1 * n1) voxel planes."""
+    n = (n1, n_other, n_other)
+    rho = np.zeros(n)
+    rho[: int(round(frac1 * n1))] = 1.0
+    Q = np.array([[k, 0.0, 0.0] for k in kx])
+    return Workload("laminate", "sc", n, M, 6, Q, rho, 1.0, (1,), 0)
+
+
+def random_design(n, rng, low=0.05, high=0.95) -> np.ndarray:
+    return rng.uniform(low, high, size=tuple(n))
