@@ -1,0 +1,172 @@
+/*
+ * phononic.h -- C ABI of the GB300 library for mixed-variational plane-wave band
+ * structures of 3-D two-phase phononic crystals and their adjoint design
+ * sensitivities (Lu, Yang, Guest, Srivastava, "3-D phononic crystals with
+ * ultra-wide band gaps").
+ *
+ * Conventions for every call below:
+ *  - All pointers named *_dev are CUDA device pointers owned by the caller; *_host
+ *    are host pointers owned by the caller.  The library never frees caller memory.
+ *  - GPU work is enqueued asynchronously on the caller's stream (a cudaStream_t
+ *    passed as void*; NULL is the legacy default stream).  Results are valid once
+ *    that stream has been synchronised.
+ *  - Return value: PC_OK (0) or a PC_E* code; pc_strerror() names it.  Argument
+ *    errors are detected on the host before anything is enqueued.  Errors found on
+ *    the device (non-convergence, bad densities, expired bounded waits) are
+ *    recorded in a device status word and reported by pc_get_stats().
+ *  - Every workspace is allocated by pc_create / pc_set_kpoints; pc_set_design,
+ *    pc_bands and pc_gap_and_grad allocate nothing.
+ *  - Units: SI.  Lattice constant a in metres, densities kg/m^3, moduli Pa.
+ */
+#ifndef PHONONIC_H
+#define PHONONIC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define PC_OK        0
+#define PC_EINVAL    1  /* bad enum, size or material constant */
+#define PC_EALIAS    2  /* a grid dimension n_i < 2M+1: plane waves alias on the centroids */
+#define PC_ENOMEM    3  /* device allocation failed */
+#define PC_ECUDA     4  /* a CUDA runtime call failed */
+#define PC_ESTATE    5  /* call out of order (e.g. pc_bands before pc_set_design) */
+#define PC_ENOCONV   6  /* device status: eigensolver hit max_iter for some k (outputs written) */
+#define PC_EDOMAIN   7  /* device status: a density outside [0,1] or not finite */
+#define PC_ETIMEOUT  8  /* device status: a bounded device-side wait expired */
+
+/* Lattices (Methods, "Study of cubic unit cells"): primitive cells of the cubic
+ * Bravais lattices, vectors along the cube edges (SC), body diagonals (BCC) and
+ * face diagonals (FCC). */
+#define PC_SC   0
+#define PC_BCC  1
+#define PC_FCC  2
+
+/* Arithmetic of the eigensolver. */
+#define PC_FP64   0  /* every step in FP64 on CUDA cores */
+#define PC_MIXED  1  /* split-BF16 tensor-core operator, FP32 block iteration,
+                        FP64 Rayleigh-Ritz and stresses at the end */
+
+/* Objective modes of pc_gap_and_grad. */
+#define PC_GAP_OMEGA      0  /* gap = 2(b-a)/(b+a) in omega = sqrt(lambda) (Results, note on gaps) */
+#define PC_GAP_LAMBDA     1  /* same in lambda = omega^2 (Methods, eq. obj) */
+#define PC_GRAD_ALLBANDS  2  /* gap_dev <- sum w*lambda, grad <- sum_{k,b} w[k,b] dlambda_{k,b}/drho_e */
+
+typedef struct pc_ctx pc_ctx;
+
+typedef struct {
+  double rho;  /* mass density, kg/m^3 (> 0) */
+  double E;    /* Young's modulus, Pa (> 0) */
+  double nu;   /* Poisson ratio, in (-1, 0.5) */
+} pc_material;
+
+typedef struct {
+  int lattice;          /* PC_SC | PC_BCC | PC_FCC */
+  double a;             /* cubic lattice constant, m (> 0) */
+  int n[3];             /* voxel grid along a1, a2, a3; voxel (i,j,l) at index (i*n1+j)*n2+l */
+  int M;                /* plane-wave index range -M..M per axis; N = (2M+1)^3 waves */
+  pc_material phase1;   /* the phase at rho_e = 1 */
+  pc_material phase0;   /* the phase at rho_e = 0 */
+  double penal;         /* chi = rho^penal (>= 1); density and compliance are linear in chi */
+  int nbands;           /* lowest bands returned per k, 1..24, and nbands <= 3N/3 */
+  int precision;        /* PC_FP64 | PC_MIXED */
+  double tol;           /* relative residual target of the block iteration (0: default) */
+  int max_iter;         /* iteration cap (0: default); hitting it sets PC_ENOCONV */
+} pc_params;
+
+typedef struct {
+  int status;              /* first device error code seen (PC_OK if none) */
+  int iterations;          /* block iterations of the last pc_bands */
+  int unconverged_k;       /* k-points above tolerance when the iteration stopped */
+  int nk;                  /* k-points set */
+  int N;                   /* plane waves */
+  int block;               /* block width m (bands + guard vectors) */
+  double max_residual;     /* largest relative residual over the returned bands */
+  double ms_setup;         /* last pc_set_design, device time */
+  double ms_bands;         /* last pc_bands, device time */
+  double ms_grad;          /* last pc_gap_and_grad, device time */
+} pc_stats;
+
+/* Creates a context: validates the parameters and allocates every per-design
+ * workspace (structure factors, the three N x N Toeplitz operators, the two
+ * inverse compliance operators, adjoint scratch).
+ * Paper: Results, eqs. mixedvariation-matrixform; Methods, eqs. loop and
+ * matrixofintegral (the k-independent element-sum matrices).
+ * Errors: PC_EINVAL, PC_EALIAS, PC_ENOMEM, PC_ECUDA.  *out is NULL on error. */
+int pc_create(const pc_params* params, pc_ctx** out);
+
+/* Sets the Bloch wavevectors: q_reduced_host holds nk rows of (Q1, Q2, Q3), the
+ * reduced coordinates of the paper's K = T1 (Q1 + alpha) + T2 (Q2 + beta) + T3 (Q3 + gamma)
+ * (reciprocal basis without 2 pi).  Allocates the block-iteration workspaces for nk
+ * points (synchronous; not for use inside stream capture).
+ * Errors: PC_EINVAL (nk < 1 or NULL), PC_ENOMEM. */
+int pc_set_kpoints(pc_ctx* ctx, const double* q_reduced_host, int nk);
+
+/* Sets the design: rho_dev holds n0*n1*n2 FP64 densities in [0, 1], C order.
+ * Enqueues: SIMP interpolation (Methods, eq. combinematerial, linear in chi = rho^p),
+ * structure factors of density and of the two compliance moduli at every plane-wave
+ * difference (eq. loop), the Toeplitz operators (eqs. intOmega, intPhi) and the two
+ * inverse compliance operators that eliminate the stress (eq. matrixform).
+ * A density outside [0, 1] sets PC_EDOMAIN in the device status.
+ * Errors: PC_EINVAL (NULL), PC_ECUDA. */
+int pc_set_design(pc_ctx* ctx, const double* rho_dev, void* stream);
+
+/* Band structure: omega_dev[k*nbands + b] = sqrt(max(lambda, 0)) in rad/s for the
+ * lowest nbands eigenvalues of H Phi^-1 H^* U = lambda Omega U (eq. matrixform) at
+ * every k, ascending.  Keeps the eigenvectors and stresses for pc_gap_and_grad.
+ * Errors: PC_ESTATE (no design or no k-points), PC_EINVAL (NULL), PC_ECUDA. */
+int pc_bands(pc_ctx* ctx, double* omega_dev, void* stream);
+
+/* Normalized gap between 1-based bands n_lower and n_lower+1 over all k (Methods,
+ * eq. obj; omega form by default) and its adjoint gradient (eqs. normalev,
+ * sensitivityew, diffOmega, diffPhi).  gap_dev: one double.  grad_dev: n0*n1*n2
+ * doubles dG/drho_e, or NULL to skip the gradient.  The max/min pick the extremal
+ * (k, band); equal values at different k take the lowest k; bands within a relative
+ * 1e-8 of the extremal one at that k share its weight equally.  For PC_GRAD_ALLBANDS,
+ * w_dev holds nk*nbands weights, n_lower is ignored, gap_dev receives sum w*lambda
+ * and grad_dev sum_{k,b} w[k,b] dlambda_{k,b}/drho_e.
+ * Errors: PC_ESTATE (pc_bands not run), PC_EINVAL (n_lower out of 1..nbands-1,
+ * bad mode, NULL w_dev for PC_GRAD_ALLBANDS), PC_ECUDA. */
+int pc_gap_and_grad(pc_ctx* ctx, int n_lower, int mode, const double* w_dev,
+                    double* gap_dev, double* grad_dev, void* stream);
+
+/* Synchronises the device and fills *out; returns out->status as well. */
+int pc_get_stats(pc_ctx* ctx, pc_stats* out);
+
+/* Resets the device status word to PC_OK. */
+int pc_clear_status(pc_ctx* ctx);
+
+/* Frees every workspace.  NULL is allowed. */
+void pc_destroy(pc_ctx* ctx);
+
+/* Static string naming a return code. */
+const char* pc_strerror(int code);
+
+/* --- Inspection entry points (used by the parity tests; not on the hot path) --- */
+
+#define PC_EXPORT_SFAC   0  /* 3 x (4M+1)^3 complex: structure factors of rho, f1, f2 (interleaved re,im) */
+#define PC_EXPORT_TOEP   1  /* 3 x N x N complex: Toeplitz operators of rho, f1, f2, SI (element sums) */
+#define PC_EXPORT_WINV   2  /* 2 x N x N complex: inverses of the f1 and f2 Toeplitz operators, SI */
+#define PC_EXPORT_EIGVEC 3  /* nk x nbands x 3N complex: eigenvectors, theta^H Omega theta = 1, SI */
+#define PC_EXPORT_LAMBDA 4  /* nk x nbands doubles: eigenvalues lambda = omega^2, SI */
+#define PC_EXPORT_WEIGHT 5  /* nk x nbands doubles: gap weights dG/dlambda of the last pc_gap_and_grad */
+
+/* Copies an internal array to host memory (synchronous).  Returns the number of
+ * doubles the array holds in *count; copies only when host != NULL and
+ * capacity >= *count.  Errors: PC_EINVAL (bad which), PC_ESTATE (not computed yet). */
+int pc_export(pc_ctx* ctx, int which, double* host, long long capacity, long long* count);
+
+/* Applies the condensed operator and the mass operator at wavevector index k to
+ * ncols vectors: x_dev, ax_dev, ox_dev hold ncols x 3N complex (interleaved),
+ * component-major within a vector (u1 over all waves, then u2, then u3).
+ * ax = H Phi^-1 H^* x and ox = Omega x (eq. matrixform), SI units, computed with the
+ * FP64 operator path.  Requires pc_set_design and pc_set_kpoints.
+ * Errors: PC_EINVAL, PC_ESTATE, PC_ECUDA. */
+int pc_apply_operator(pc_ctx* ctx, int k, int ncols, const double* x_dev,
+                      double* ax_dev, double* ox_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHONONIC_H */

@@ -1,0 +1,182 @@
+"""ctypes binding of libphononic.so: the C entry points under their own names, plus a thin
+torch-facing wrapper.  Argument marshalling only: every step of the band and adjoint
+path runs in the library's CUDA kernels.  Importing this module raises if the library
+has not been built; there is no fallback."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libphononic.so")
+
+PC_OK, PC_EINVAL, PC_EALIAS, PC_ENOMEM, PC_ECUDA, PC_ESTATE, PC_ENOCONV, PC_EDOMAIN, PC_ETIMEOUT = range(9)
+PC_SC, PC_BCC, PC_FCC = 0, 1, 2
+PC_FP64, PC_MIXED = 0, 1
+PC_GAP_OMEGA, PC_GAP_LAMBDA, PC_GRAD_ALLBANDS = 0, 1, 2
+PC_EXPORT_SFAC, PC_EXPORT_TOEP, PC_EXPORT_WINV, PC_EXPORT_EIGVEC, PC_EXPORT_LAMBDA, PC_EXPORT_WEIGHT = range(6)
+LATTICES = {"sc": PC_SC, "bcc": PC_BCC, "fcc": PC_FCC}
+
+
+class pc_material(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("E", ctypes.c_double), ("nu", ctypes.c_double)]
+
+
+class pc_params(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int),
+        ("a", ctypes.c_double),
+        ("n", ctypes.c_int * 3),
+        ("M", ctypes.c_int),
+        ("phase1", pc_material),
+        ("phase0", pc_material),
+        ("penal", ctypes.c_double),
+        ("nbands", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+    ]
+
+
+class pc_stats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("iterations", ctypes.c_int),
+        ("unconverged_k", ctypes.c_int),
+        ("nk", ctypes.c_int),
+        ("N", ctypes.c_int),
+        ("block", ctypes.c_int),
+        ("max_residual", ctypes.c_double),
+        ("ms_setup", ctypes.c_double),
+        ("ms_bands", ctypes.c_double),
+        ("ms_grad", ctypes.c_double),
+    ]
+
+
+EXPORTED = ["pc_create", "pc_set_kpoints", "pc_set_design", "pc_bands", "pc_gap_and_grad", "pc_get_stats",
+            "pc_clear_status", "pc_destroy", "pc_strerror", "pc_export", "pc_apply_operator"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the compiled library (raises OSError when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: run paper_1603_06855_gb300.build_lib.build() first")
+    lib = ctypes.CDLL(path)
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    lib.pc_create.argtypes = [ctypes.POINTER(pc_params), ctypes.POINTER(P)]
+    lib.pc_set_kpoints.argtypes = [P, P, I]
+    lib.pc_set_design.argtypes = [P, P, P]
+    lib.pc_bands.argtypes = [P, P, P]
+    lib.pc_gap_and_grad.argtypes = [P, I, I, P, P, P, P]
+    lib.pc_get_stats.argtypes = [P, ctypes.POINTER(pc_stats)]
+    lib.pc_clear_status.argtypes = [P]
+    lib.pc_destroy.argtypes = [P]
+    lib.pc_destroy.restype = None
+    lib.pc_strerror.argtypes = [I]
+    lib.pc_strerror.restype = ctypes.c_char_p
+    lib.pc_export.argtypes = [P, I, P, LL, ctypes.POINTER(LL)]
+    lib.pc_apply_operator.argtypes = [P, I, I, P, P, P, P]
+    for name in EXPORTED:
+        if name not in ("pc_destroy", "pc_strerror"):
+            getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def pc_strerror(code: int) -> str:
+    return load().pc_strerror(code).decode()
+
+
+class PhononicError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {pc_strerror(code)} ({code})")
+        self.code = code
+
+
+def _check(rc: int, where: str):
+    if rc != PC_OK:
+        raise PhononicError(rc, where)
+
+
+def make_params(lattice, n, M, nbands, phase1, phase0, penal=1.0, precision=PC_FP64, a=1.0, tol=0.0,
+                max_iter=0) -> pc_params:
+    p = pc_params()
+    p.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+    p.a = float(a)
+    for i in range(3):
+        p.n[i] = int(n[i])
+    p.M = int(M)
+    p.phase1 = pc_material(phase1["rho"], phase1["E"], phase1["nu"])
+    p.phase0 = pc_material(phase0["rho"], phase0["E"], phase0["nu"])
+    p.penal = float(penal)
+    p.nbands = int(nbands)
+    p.precision = int(precision)
+    p.tol = float(tol)
+    p.max_iter = int(max_iter)
+    return p
+
+
+def pc_create(params: pc_params) -> int:
+    h = ctypes.c_void_p()
+    _check(load().pc_create(ctypes.byref(params), ctypes.byref(h)), "pc_create")
+    return h.value
+
+
+def pc_create_rc(params: pc_params) -> int:
+    """Return code only (for argument-validation tests; frees any context created)."""
+    h = ctypes.c_void_p()
+    rc = load().pc_create(ctypes.byref(params), ctypes.byref(h))
+    if rc == PC_OK and h.value:
+        load().pc_destroy(h)
+    return rc
+
+
+def pc_set_kpoints(ctx: int, q_host) -> None:
+    import numpy as np
+    q = np.ascontiguousarray(q_host, dtype=np.float64)
+    _check(load().pc_set_kpoints(ctx, q.ctypes.data, q.shape[0]), "pc_set_kpoints")
+
+
+def pc_set_design(ctx: int, rho_ptr: int, stream: int = 0) -> None:
+    _check(load().pc_set_design(ctx, rho_ptr, stream), "pc_set_design")
+
+
+def pc_bands(ctx: int, omega_ptr: int, stream: int = 0) -> None:
+    _check(load().pc_bands(ctx, omega_ptr, stream), "pc_bands")
+
+
+def pc_gap_and_grad(ctx: int, n_lower: int, mode: int, w_ptr: int, gap_ptr: int, grad_ptr: int,
+                    stream: int = 0) -> None:
+    _check(load().pc_gap_and_grad(ctx, n_lower, mode, w_ptr, gap_ptr, grad_ptr, stream), "pc_gap_and_grad")
+
+
+def pc_get_stats(ctx: int) -> pc_stats:
+    st = pc_stats()
+    load().pc_get_stats(ctx, ctypes.byref(st))
+    return st
+
+
+def pc_clear_status(ctx: int) -> None:
+    _check(load().pc_clear_status(ctx), "pc_clear_status")
+
+
+def pc_destroy(ctx: int) -> None:
+    load().pc_destroy(ctx)
+
+
+def pc_export(ctx: int, which: int):
+    import numpy as np
+    n = ctypes.c_longlong()
+    _check(load().pc_export(ctx, which, None, 0, ctypes.byref(n)), "pc_export")
+    out = np.empty(n.value, dtype=np.float64)
+    _check(load().pc_export(ctx, which, out.ctypes.data, n.value, ctypes.byref(n)), "pc_export")
+    return out
+
+
+def pc_apply_operator(ctx: int, k: int, ncols: int, x_ptr: int, ax_ptr: int, ox_ptr: int, stream: int = 0):
+    _check(load().pc_apply_operator(ctx, k, ncols, x_ptr, ax_ptr, ox_ptr, stream), "pc_apply_operator")

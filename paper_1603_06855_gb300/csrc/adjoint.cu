@@ -1,0 +1,229 @@
+// Gap objective (Methods, eq. obj; omega form of the Results' note on normalized gaps)
+// and the adjoint design sensitivities (Methods, eqs. normalev, sensitivityew, diffOmega,
+// diffPhi).  With theta^H Omega theta = 1 and s = Phi^-1 H^H theta,
+//   d lambda / d rho_e = chi'_e v_e [ -lambda (rho1 - rho0) sum_c |u_c(x_e)|^2
+//                                      - (f1_1 - f1_0) |sigma_bulk(x_e)|^2 - (f2_1 - f2_0) |sigma_dev(x_e)|^2 ],
+// where u and sigma are the displacement and stress fields synthesised at the element
+// centroid from the plane-wave coefficients.  The kernels synthesise the 3 + 6 fields of
+// every weighted (k, band) on the voxel grid by separable sums (axis 2, axis 1 into a
+// scratch array, then axis 0 inside the per-voxel reduction) and reduce the weighted
+// quadratic forms over all (k, band).
+#include "kernels.h"
+
+// ---------------------------------------------------------------------------
+__global__ void k_omega(const double* __restrict__ lam_m, int nk, int nb, int m, double lref,
+                        double* __restrict__ omega, double* __restrict__ lam_phys, double* __restrict__ lam_nd) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nk * nb) return;
+  int k = t / nb, b = t % nb;
+  double l = lam_m[k * m + b];
+  if (lam_nd) lam_nd[t] = l;
+  if (lam_phys) lam_phys[t] = l * lref;
+  if (omega) omega[t] = sqrt(fmax(l * lref, 0.0));
+}
+int launch_omega(const double* lam_m, int nk, int nb, int m, double lref, double* omega, double* lam_nd,
+                 cudaStream_t s) {
+  k_omega<<<cdiv((long long)nk * nb, 256), 256, 0, s>>>(lam_m, nk, nb, m, lref, omega, nullptr, lam_nd);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Gap, weights dG/dlambda (physical) and the compacted list of weighted (k, band).
+__global__ void k_gap(GapArgs a) {
+  __shared__ double sv[256];
+  __shared__ int si[256];
+  __shared__ int ka_s, kb_s;
+  const int nk = a.nk, nb = a.nb;
+  for (int t = threadIdx.x; t < nk * nb; t += blockDim.x) a.weights[t] = 0.0;
+  __syncthreads();
+  if (a.mode == PC_GRAD_ALLBANDS) {
+    double s = 0.0;
+    for (int t = threadIdx.x; t < nk * nb; t += blockDim.x) {
+      a.weights[t] = a.w_user[t];
+      s += a.w_user[t] * a.lam[t] * a.lref;
+    }
+    sv[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) sv[threadIdx.x] += sv[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      *a.gap_out = sv[0];
+      int c = 0;
+      for (int t = 0; t < nk * nb; ++t)
+        if (a.weights[t] != 0.0) a.pairs[c++] = t;
+      *a.npairs = c;
+    }
+    return;
+  }
+  const int lo = a.n_lower - 1, hi = a.n_lower;
+  // argmax_k lam[k][lo], lowest k among ties
+  double bv = -1e300;
+  int bi = 0x7fffffff;
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    double v = a.lam[k * nb + lo];
+    if (v > bv || (v == bv && k < bi)) { bv = v; bi = k; }
+  }
+  sv[threadIdx.x] = bv; si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      double v2 = sv[threadIdx.x + w]; int i2 = si[threadIdx.x + w];
+      if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) { sv[threadIdx.x] = v2; si[threadIdx.x] = i2; }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ka_s = si[0];
+  __syncthreads();
+  // argmin_k lam[k][hi], lowest k among ties
+  bv = 1e300; bi = 0x7fffffff;
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    double v = a.lam[k * nb + hi];
+    if (v < bv || (v == bv && k < bi)) { bv = v; bi = k; }
+  }
+  sv[threadIdx.x] = bv; si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      double v2 = sv[threadIdx.x + w]; int i2 = si[threadIdx.x + w];
+      if (v2 < sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) { sv[threadIdx.x] = v2; si[threadIdx.x] = i2; }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) kb_s = si[0];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  int ka = ka_s, kb = kb_s;
+  double la = a.lam[ka * nb + lo] * a.lref, lb = a.lam[kb * nb + hi] * a.lref;
+  double G, wa, wb;
+  if (a.mode == PC_GAP_OMEGA) {
+    double A_ = sqrt(fmax(la, 0.0)), B_ = sqrt(fmax(lb, 0.0));
+    G = 2.0 * (B_ - A_) / (B_ + A_);
+    wa = A_ > 0.0 ? -2.0 * B_ / (A_ * (A_ + B_) * (A_ + B_)) : 0.0;
+    wb = B_ > 0.0 ? 2.0 * A_ / (B_ * (A_ + B_) * (A_ + B_)) : 0.0;
+  } else {
+    G = 2.0 * (lb - la) / (lb + la);
+    wa = -4.0 * lb / ((la + lb) * (la + lb));
+    wb = 4.0 * la / ((la + lb) * (la + lb));
+  }
+  *a.gap_out = G;
+  int c = 0;
+  for (int side = 0; side < 2; ++side) {
+    int k = side == 0 ? ka : kb;
+    int band = side == 0 ? lo : hi;
+    double wt = side == 0 ? wa : wb;
+    double ref = a.lam[k * nb + band];
+    int members = 0;
+    for (int b = 0; b < nb; ++b) members += (fabs(a.lam[k * nb + b] - ref) <= a.rel_tol * fabs(ref)) ? 1 : 0;
+    for (int b = 0; b < nb; ++b)
+      if (fabs(a.lam[k * nb + b] - ref) <= a.rel_tol * fabs(ref)) a.weights[k * nb + b] += wt / members;
+  }
+  for (int t = 0; t < nk * nb; ++t)
+    if (a.weights[t] != 0.0) a.pairs[c++] = t;
+  *a.npairs = c;
+}
+int launch_gap(const GapArgs& a, cudaStream_t s) {
+  k_gap<<<1, 256, 0, s>>>(a);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Axis-2 and axis-1 synthesis of field f of pair p:
+//   t2[p][f][g1][j][l] = sum_{g2,g3} c[g1][g2][g3] e^{i pi G2 (2j+1)/n1} e^{i pi G3 (2l+1)/n2}
+// f < 3: displacement component f of theta; f >= 3: stress coordinate f-3.
+__global__ void k_adj_synth12(AdjointArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int p = blockIdx.x, f = blockIdx.y;
+  if (p >= *a.npairs) return;
+  const int M2 = 2 * a.M + 1, N = a.N, n1 = a.n1, n2 = a.n2;
+  double2* c = (double2*)smem;             // N
+  double2* t1 = c + N;                     // M2*M2*n2
+  double2* ph3 = t1 + M2 * M2 * n2;        // M2*n2
+  double2* ph2 = ph3 + M2 * n2;            // M2*n1
+  const int pr = a.pairs[p];
+  const int k = pr / a.nb, b = pr % a.nb;
+  const long long vec = (long long)k * a.m + b;
+  const long long nvec = (long long)a.nk * a.m;
+  const double2* src = (f < 3) ? a.theta + (vec * 3 + f) * N : a.sig + ((long long)(f - 3) * nvec + vec) * N;
+  for (int q = threadIdx.x; q < N; q += blockDim.x) c[q] = src[q];
+  for (int t = threadIdx.x; t < M2 * n2; t += blockDim.x) {
+    int g = t / n2, l = t % n2;
+    ph3[t] = phase_pi_over((long long)(g - a.M) * (2 * l + 1), n2);
+  }
+  for (int t = threadIdx.x; t < M2 * n1; t += blockDim.x) {
+    int g = t / n1, j = t % n1;
+    ph2[t] = phase_pi_over((long long)(g - a.M) * (2 * j + 1), n1);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < M2 * M2 * n2; t += blockDim.x) {
+    int g12 = t / n2, l = t % n2;
+    double2 s = make_double2(0.0, 0.0);
+    for (int g3 = 0; g3 < M2; ++g3) cfma(s, c[g12 * M2 + g3], ph3[g3 * n2 + l]);
+    t1[t] = s;
+  }
+  __syncthreads();
+  double2* out = a.t2 + ((long long)p * 9 + f) * M2 * n1 * n2;
+  for (long long t = threadIdx.x; t < (long long)M2 * n1 * n2; t += blockDim.x) {
+    int l = (int)(t % n2);
+    int j = (int)((t / n2) % n1);
+    int g1 = (int)(t / ((long long)n1 * n2));
+    double2 s = make_double2(0.0, 0.0);
+    for (int g2 = 0; g2 < M2; ++g2) cfma(s, t1[(g1 * M2 + g2) * n2 + l], ph2[g2 * n1 + j]);
+    out[t] = s;
+  }
+}
+
+// Axis-0 synthesis fused with the weighted reduction over (k, band).
+__global__ void k_adj_reduce(AdjointArgs a) {
+  const int n0 = a.n0, n1 = a.n1, n2 = a.n2, M2 = 2 * a.M + 1;
+  const int j = blockIdx.y;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n0 * n2) return;
+  const int i = v / n2, l = v % n2;
+  double2 ph[11];
+  for (int g = 0; g < M2; ++g) ph[g] = phase_pi_over((long long)(g - a.M) * (2 * i + 1), n0);
+  const int np = *a.npairs;
+  const long long fstride = (long long)M2 * n1 * n2;
+  const long long gstride = (long long)n1 * n2;
+  double acc = 0.0;
+  for (int p = 0; p < np; ++p) {
+    const int pr = a.pairs[p];
+    const double w = a.weights[pr];
+    const double lam = a.lam[pr] * a.lref;
+    const double2* base = a.t2 + (long long)p * 9 * fstride + (long long)j * n2 + l;
+    double q[9];
+    for (int f = 0; f < 9; ++f) {
+      double2 s = make_double2(0.0, 0.0);
+      const double2* src = base + f * fstride;
+      for (int g = 0; g < M2; ++g) cfma(s, src[g * gstride], ph[g]);
+      q[f] = s.x * s.x + s.y * s.y;
+    }
+    double u2 = q[0] + q[1] + q[2];
+    double sd = q[4] + q[5] + q[6] + q[7] + q[8];
+    acc += w * (-lam * a.d_rho * u2 - a.two_pi_V_sq * (a.d_f1 * q[3] + a.d_f2 * sd));
+  }
+  const long long e = ((long long)i * n1 + j) * n2 + l;
+  a.grad[e] = acc * a.inv_sO * a.ve * a.dchi[e];
+}
+
+int launch_adjoint(const AdjointArgs& a, cudaStream_t s) {
+  const int M2 = 2 * a.M + 1;
+  if (M2 > 11) return PC_EINVAL;
+  size_t sm = sizeof(double2) * ((size_t)a.N + (size_t)M2 * M2 * a.n2 + (size_t)M2 * a.n2 + (size_t)M2 * a.n1);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_adj_synth12, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  if (sm > 200 * 1024) return PC_EINVAL;
+  dim3 g1(a.max_pairs, 9);
+  k_adj_synth12<<<g1, 256, sm, s>>>(a);
+  PC_LAUNCH_CHECK();
+  dim3 g2(cdiv((long long)a.n0 * a.n2, 256), a.n1);
+  k_adj_reduce<<<g2, 256, 0, s>>>(a);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}

@@ -1,0 +1,659 @@
+// Batched block operations of the locally optimal block preconditioned conjugate
+// gradient iteration (one independent problem per k-point), and the small projected
+// problems solved one CTA per k:
+//   gram   -- G = A^H B over the 3N rows, for up to three m-column blocks per side
+//   update -- out = [S_0 S_1 S_2] C for up to three operand triplets sharing C
+//   small_rr   -- the projected pencil (GA, GO): unit-diagonal scaling, Cholesky of GO that
+//                 drops dependent columns, reduction to standard form, cyclic Jacobi,
+//                 lowest m Ritz pairs
+//   small_chol -- Cholesky-QR transform T with T^H G T = I (dependent columns -> zero)
+#include "kernels.h"
+
+#define GRAM_ROWS 16
+#define GRAM_SPLIT 8
+
+int g_acc64 = 0;  // experiment switch: FP64 accumulation in the FP32 Gram and update kernels
+
+
+template <typename R, typename RA>
+__global__ __launch_bounds__(256) void k_gram(BlockList<R> A, int na, BlockList<R> B, int nbk, int m, int n3,
+                                              typename cplx_t<R>::type* __restrict__ part) {
+  typedef typename cplx_t<R>::type C2;
+  typedef typename cplx_t<RA>::type CA;
+  __shared__ C2 sA[GRAM_ROWS][72];
+  __shared__ C2 sB[GRAM_ROWS][72];
+  const int k = blockIdx.x, split = blockIdx.y;
+  const int ca = na * m, cb = nbk * m;
+  const long long kofs = (long long)k * m * n3;
+  int chunk = (n3 + GRAM_SPLIT - 1) / GRAM_SPLIT;
+  int r_begin = split * chunk, r_end = min(n3, r_begin + chunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  CA acc[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) acc[i][j] = mk<RA>(0, 0);
+  for (int r0 = r_begin; r0 < r_end; r0 += GRAM_ROWS) {
+    for (int t = threadIdx.x; t < GRAM_ROWS * ca; t += 256) {
+      int rr = t % GRAM_ROWS, col = t / GRAM_ROWS;
+      int r = r0 + rr;
+      sA[rr][col] = (r < r_end) ? A.p[col / m][kofs + (long long)(col % m) * n3 + r] : mk<R>(0, 0);
+    }
+    for (int t = threadIdx.x; t < GRAM_ROWS * cb; t += 256) {
+      int rr = t % GRAM_ROWS, col = t / GRAM_ROWS;
+      int r = r0 + rr;
+      sB[rr][col] = (r < r_end) ? B.p[col / m][kofs + (long long)(col % m) * n3 + r] : mk<R>(0, 0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < GRAM_ROWS; ++rr) {
+      C2 a[5], b[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) { int c = tx + 16 * i; a[i] = c < ca ? sA[rr][c] : mk<R>(0, 0); }
+#pragma unroll
+      for (int j = 0; j < 5; ++j) { int c = ty + 16 * j; b[j] = c < cb ? sB[rr][c] : mk<R>(0, 0); }
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) cfmac(acc[i][j], mk<RA>(a[i].x, a[i].y), mk<RA>(b[j].x, b[j].y));
+    }
+    __syncthreads();
+  }
+  C2* out = part + ((long long)k * GRAM_SPLIT + split) * ca * cb;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      int a_ = tx + 16 * i, b_ = ty + 16 * j;
+      if (a_ < ca && b_ < cb) out[a_ * cb + b_] = mk<R>((R)acc[i][j].x, (R)acc[i][j].y);
+    }
+}
+
+template <typename R>
+__global__ void k_gram_reduce(const typename cplx_t<R>::type* __restrict__ part, int nel, R scale,
+                              typename cplx_t<R>::type* __restrict__ G) {
+  typedef typename cplx_t<R>::type C2;
+  int k = blockIdx.y;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nel) return;
+  const C2* p = part + (long long)k * GRAM_SPLIT * nel + e;
+  C2 s = mk<R>(0, 0);
+  for (int i = 0; i < GRAM_SPLIT; ++i) s = cadd(s, p[(long long)i * nel]);
+  G[(long long)k * nel + e] = cscale(s, scale);
+}
+
+template <typename R>
+int launch_gram(BlockList<R> A, int na, BlockList<R> B, int nbk, int nk, int m, int n3, R scale,
+                typename cplx_t<R>::type* part, typename cplx_t<R>::type* G, cudaStream_t s) {
+  if (na * m > 72 || nbk * m > 72 || na * m > 80) return PC_EINVAL;
+  dim3 grid(nk, GRAM_SPLIT);
+  if (g_acc64) k_gram<R, double><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
+  else k_gram<R, R><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
+  PC_LAUNCH_CHECK();
+  int nel = na * m * nbk * m;
+  dim3 g2(cdiv(nel, 256), nk);
+  k_gram_reduce<R><<<g2, 256, 0, s>>>(part, nel, scale, G);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+template int launch_gram<double>(BlockList<double>, int, BlockList<double>, int, int, int, int, double, double2*, double2*, cudaStream_t);
+template int launch_gram<float>(BlockList<float>, int, BlockList<float>, int, int, int, int, float, float2*, float2*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// out[t][k][j][r] = (identity_last ? in[t][last][k][j][r] : 0) + sum_b sum_i in[t][b][k][i][r] C[k][b*m+i][j]
+// One thread per row r: every row of every output is written by the thread that read it,
+// so the output may alias the last input block.
+template <typename R, int MOUT, typename RA>
+__global__ __launch_bounds__(128) void k_update(UpdateArgs<R> a) {
+  typedef typename cplx_t<R>::type C2;
+  typedef typename cplx_t<RA>::type CA;
+  __shared__ C2 sC[72 * 24];
+  const int k = blockIdx.y, t = blockIdx.z;
+  const int nsum = a.identity_last ? a.nblk - 1 : a.nblk;
+  const int rows = nsum * a.m;
+  const C2* Ck = a.C + (long long)k * a.cstride;
+  for (int e = threadIdx.x; e < rows * a.mout; e += blockDim.x) {
+    int i = e / a.mout, j = e % a.mout;
+    sC[e] = Ck[(long long)i * a.cld + j];
+  }
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.n3) return;
+  CA acc[MOUT];
+#pragma unroll
+  for (int j = 0; j < MOUT; ++j) acc[j] = mk<RA>(0, 0);
+  if (a.identity_last) {
+    const C2* src = a.in[t][a.nblk - 1] + (long long)k * a.in_kstride + r;
+#pragma unroll
+    for (int j = 0; j < MOUT; ++j)
+      if (j < a.mout) { C2 v = src[(long long)j * a.n3]; acc[j] = mk<RA>(v.x, v.y); }
+  }
+  for (int b = 0; b < nsum; ++b) {
+    const C2* src = a.in[t][b] + (long long)k * a.in_kstride + r;
+    for (int i = 0; i < a.m; ++i) {
+      C2 v = src[(long long)i * a.n3];
+      CA va = mk<RA>(v.x, v.y);
+      const C2* crow = sC + (b * a.m + i) * a.mout;
+#pragma unroll
+      for (int j = 0; j < MOUT; ++j)
+        if (j < a.mout) cfma(acc[j], va, mk<RA>(crow[j].x, crow[j].y));
+    }
+  }
+  C2* dst = a.out[t] + (long long)k * a.out_kstride + r;
+#pragma unroll
+  for (int j = 0; j < MOUT; ++j)
+    if (j < a.mout) dst[(long long)j * a.n3] = mk<R>((R)acc[j].x, (R)acc[j].y);
+}
+
+template <typename R> int launch_update(const UpdateArgs<R>& a, cudaStream_t s) {
+  int nsum = a.identity_last ? a.nblk - 1 : a.nblk;
+  if (nsum * a.m * a.mout > 72 * 24 || a.mout > 24) return PC_EINVAL;
+  dim3 grid(cdiv(a.n3, 128), a.nk, a.ntrip);
+  if (g_acc64) {
+    if (a.mout <= 8) k_update<R, 8, double><<<grid, 128, 0, s>>>(a);
+    else if (a.mout <= 16) k_update<R, 16, double><<<grid, 128, 0, s>>>(a);
+    else k_update<R, 24, double><<<grid, 128, 0, s>>>(a);
+  } else {
+    if (a.mout <= 8) k_update<R, 8, R><<<grid, 128, 0, s>>>(a);
+    else if (a.mout <= 16) k_update<R, 16, R><<<grid, 128, 0, s>>>(a);
+    else k_update<R, 24, R><<<grid, 128, 0, s>>>(a);
+  }
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+template int launch_update<double>(const UpdateArgs<double>&, cudaStream_t);
+template int launch_update<float>(const UpdateArgs<float>&, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Small dense Hermitian algebra in shared memory, one CTA (256 threads) per problem.
+template <typename R> struct SmallEps;
+template <> struct SmallEps<double> { static constexpr double v = 2.220446049250313e-16; };
+template <> struct SmallEps<float>  { static constexpr float v = 1.1920929e-07f; };
+
+// Unit-diagonal scaling of Hermitian A (and B if given): D_i = 1/sqrt(B_ii) (0 when B_ii <= 0).
+// Cholesky of B with column dropping, in place (lower triangle); drop[j] = 1 for dropped j.
+template <typename R>
+__device__ void chol_drop(typename cplx_t<R>::type* B, int n, R tol, int* drop) {
+  typedef typename cplx_t<R>::type C2;
+  for (int j = 0; j < n; ++j) {
+    __syncthreads();
+    R d = B[j * n + j].x;
+    bool dr = !(d > tol);
+    __syncthreads();
+    if (dr) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (i != j) { B[i * n + j] = mk<R>(0, 0); B[j * n + i] = mk<R>(0, 0); }
+      if (threadIdx.x == 0) { B[j * n + j] = mk<R>(1, 0); drop[j] = 1; }
+      continue;
+    }
+    R sq = sqrt(d), inv = (R)1 / sq;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) B[i * n + j] = cscale(B[i * n + j], inv);
+    if (threadIdx.x == 0) B[j * n + j] = mk<R>(sq, 0);
+    __syncthreads();
+    int nt = n - j - 1;
+    for (int t = threadIdx.x; t < nt * nt; t += blockDim.x) {
+      int i = j + 1 + t / nt, c = j + 1 + t % nt;
+      if (c <= i) {
+        C2 v = B[i * n + c];
+        C2 l1 = B[i * n + j], l2 = B[c * n + j];
+        v.x -= l1.x * l2.x + l1.y * l2.y;
+        v.y -= l1.y * l2.x - l1.x * l2.y;
+        B[i * n + c] = v;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// In-place inverse of the lower-triangular L (n x n); upper triangle zeroed.  tmp: n entries.
+template <typename R>
+__device__ void tri_inv_lower(typename cplx_t<R>::type* L, int n, typename cplx_t<R>::type* tmp) {
+  typedef typename cplx_t<R>::type C2;
+  for (int j = n - 1; j >= 0; --j) {
+    __syncthreads();
+    C2 ljj = L[j * n + j];
+    R den = ljj.x * ljj.x + ljj.y * ljj.y;
+    C2 ajj = mk<R>(ljj.x / den, -ljj.y / den);
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) tmp[i] = L[i * n + j];
+    __syncthreads();
+    // new L[i][j] = -ajj * sum_{c=j+1..i} Linv[i][c] * old L[c][j]
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      C2 s = mk<R>(0, 0);
+      for (int c = j + 1; c <= i; ++c) cfma(s, L[i * n + c], tmp[c]);
+      C2 v = cmul(s, ajj);
+      L[i * n + j] = mk<R>(-v.x, -v.y);
+    }
+    if (threadIdx.x == 0) L[j * n + j] = ajj;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t / n, c = t % n;
+    if (c > i) L[t] = mk<R>(0, 0);
+  }
+  __syncthreads();
+}
+
+// Two-sided cyclic Jacobi on Hermitian A (n x n), accumulating V <- V J.  Pairs are
+// scheduled by the circle method so each round rotates n/2 disjoint planes in parallel.
+template <typename R>
+__device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V, int n, int max_sweeps,
+                       R* rc, typename cplx_t<R>::type* rs, int* rp, int* rq, R* red, const int* drop) {
+  typedef typename cplx_t<R>::type C2;
+  const int npad = n + (n & 1);
+  const int npairs = npad / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // convergence: off-diagonal mass vs total
+    R off = 0, tot = 0;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      int i = t / n, c = t % n;
+      if (drop[i] || drop[c]) continue;
+      R v = A[t].x * A[t].x + A[t].y * A[t].y;
+      tot += v;
+      if (i != c) off += v;
+    }
+    red[threadIdx.x] = off;
+    red[blockDim.x + threadIdx.x] = tot;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) { red[threadIdx.x] += red[threadIdx.x + w]; red[blockDim.x + threadIdx.x] += red[blockDim.x + threadIdx.x + w]; }
+      __syncthreads();
+    }
+    R eps = SmallEps<R>::v;
+    bool done = !(red[0] > eps * eps * red[blockDim.x]);
+    __syncthreads();
+    if (done) break;
+    for (int round = 0; round < npad - 1; ++round) {
+      for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
+        int a = (t == 0) ? 0 : ((t - 1 + round) % (npad - 1)) + 1;
+        int b = ((npad - 1 - t - 1 + round) % (npad - 1)) + 1;
+        int p = min(a, b), q = max(a, b);
+        R c = 1;
+        C2 sp = mk<R>(0, 0);
+        if (q < n && !drop[p] && !drop[q]) {
+          C2 apq = A[p * n + q];
+          R beta = sqrt(apq.x * apq.x + apq.y * apq.y);
+          R app = A[p * n + p].x, aqq = A[q * n + q].x;
+          if (beta > eps * (fabs(app) + fabs(aqq)) * (R)0.01 && beta > (R)0) {
+            R tau = (aqq - app) / (2 * beta);
+            R tt = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
+            c = (R)1 / sqrt((R)1 + tt * tt);
+            R sn = tt * c;
+            sp = mk<R>(sn * apq.x / beta, sn * apq.y / beta);
+          }
+        }
+        rp[t] = p; rq[t] = q; rc[t] = c; rs[t] = sp;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int e = threadIdx.x; e < n * npairs; e += blockDim.x) {
+        int t = e % npairs, i = e / npairs;
+        int p = rp[t], q = rq[t];
+        if (q >= n) continue;
+        R c = rc[t];
+        C2 sp = rs[t];
+        if (sp.x == 0 && sp.y == 0) continue;
+        C2 sc = cconj(sp);
+        C2 aip = A[i * n + p], aiq = A[i * n + q];
+        A[i * n + p] = csub(cscale(aip, c), cmul(sc, aiq));
+        A[i * n + q] = cadd(cmul(sp, aip), cscale(aiq, c));
+        C2 vip = V[i * n + p], viq = V[i * n + q];
+        V[i * n + p] = csub(cscale(vip, c), cmul(sc, viq));
+        V[i * n + q] = cadd(cmul(sp, vip), cscale(viq, c));
+      }
+      __syncthreads();
+      // rows: A <- J^H A
+      for (int e = threadIdx.x; e < n * npairs; e += blockDim.x) {
+        int t = e % npairs, j = e / npairs;
+        int p = rp[t], q = rq[t];
+        if (q >= n) continue;
+        R c = rc[t];
+        C2 sp = rs[t];
+        if (sp.x == 0 && sp.y == 0) continue;
+        C2 apj = A[p * n + j], aqj = A[q * n + j];
+        A[p * n + j] = csub(cscale(apj, c), cmul(sp, aqj));
+        A[q * n + j] = cadd(cmul(cconj(sp), apj), cscale(aqj, c));
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+}
+
+template <typename R> struct SmallSmem {
+  static size_t bytes(int n) {
+    typedef typename cplx_t<R>::type C2;
+    return sizeof(C2) * (2 * (size_t)n * n + n + 64) + sizeof(R) * (3 * n + 64 + 512) + sizeof(int) * (3 * n + 128);
+  }
+};
+
+template <typename R>
+__global__ __launch_bounds__(256) void k_small_rr(const typename cplx_t<R>::type* __restrict__ GA,
+                                                  const typename cplx_t<R>::type* __restrict__ GO, int n, int m,
+                                                  R drop_tol, const int* __restrict__ kdone, R* __restrict__ lam_out,
+                                                  typename cplx_t<R>::type* __restrict__ coef, int* status) {
+  typedef typename cplx_t<R>::type C2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  C2* A = (C2*)smem;                 // n*n
+  C2* B = A + n * n;                 // n*n
+  C2* tmp = B + n * n;               // n
+  C2* rs = tmp + n;                  // 64
+  R* D = (R*)(rs + 64);              // n
+  R* ev = D + n;                     // n
+  R* rc = ev + n;                    // 64
+  R* red = rc + 64;                  // 512
+  R* spare = red + 512;              // n
+  int* drop = (int*)(spare + n);     // n
+  int* perm = drop + n;              // n
+  int* rp = perm + n;                // 64
+  int* rq = rp + 64;                 // 64
+  int* cnt = rq + 64;
+  (void)spare;
+  const int k = blockIdx.x;
+  const C2* ga = GA + (long long)k * n * n;
+  const C2* go = GO + (long long)k * n * n;
+  if (kdone && kdone[k]) {  // locked k-point: keep its block, leave lambda untouched
+    C2* ck = coef + (long long)k * n * m;
+    for (int t = threadIdx.x; t < n * m; t += blockDim.x) {
+      int i = t / m, j = t % m;
+      ck[t] = (i == j) ? mk<R>(1, 0) : mk<R>(0, 0);
+    }
+    return;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    R d = go[i * n + i].x;
+    D[i] = (d > (R)0 && d == d) ? (R)1 / sqrt(d) : (R)0;
+    drop[i] = 0;
+  }
+  __syncthreads();
+  // Hermitian-symmetrised, scaled copies
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t / n, c = t % n;
+    C2 a1 = ga[i * n + c], a2 = ga[c * n + i];
+    C2 b1 = go[i * n + c], b2 = go[c * n + i];
+    R s = D[i] * D[c] * (R)0.5;
+    A[t] = mk<R>((a1.x + a2.x) * s, (a1.y - a2.y) * s);
+    B[t] = mk<R>((b1.x + b2.x) * s, (b1.y - b2.y) * s);
+  }
+  __syncthreads();
+  chol_drop<R>(B, n, drop_tol, drop);
+  tri_inv_lower<R>(B, n, tmp);  // B = Li (lower)
+  // A <- A Li^H, row by row (one warp per row, row staged in tmp-per-warp region of V? use red as scratch)
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = warp; i < n; i += nw) {
+      // each lane computes entries j = lane, lane+32, ... of the new row i; old row read from A
+      C2 outv[3];
+      int cnt_j = 0;
+      for (int j = lane; j < n && cnt_j < 3; j += 32, ++cnt_j) {
+        C2 s = mk<R>(0, 0);
+        for (int c = 0; c <= j; ++c) cfmac(s, B[j * n + c], A[i * n + c]);  // sum_c A[i][c] conj(Li[j][c])
+        outv[cnt_j] = s;
+      }
+      __syncwarp();
+      cnt_j = 0;
+      for (int j = lane; j < n && cnt_j < 3; j += 32, ++cnt_j) A[i * n + j] = outv[cnt_j];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // A <- Li A, column by column
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = warp; j < n; j += nw) {
+      C2 outv[3];
+      int ci = 0;
+      for (int i = lane; i < n && ci < 3; i += 32, ++ci) {
+        C2 s = mk<R>(0, 0);
+        for (int c = 0; c <= i; ++c) cfma(s, B[i * n + c], A[c * n + j]);
+        outv[ci] = s;
+      }
+      __syncwarp();
+      ci = 0;
+      for (int i = lane; i < n && ci < 3; i += 32, ++ci) A[i * n + j] = outv[ci];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // dropped coordinates: decoupled; Jacobi leaves them alone and the sort puts them last
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t / n, c = t % n;
+    if (drop[i] || drop[c]) A[t] = mk<R>(0, 0);
+  }
+  __syncthreads();
+  // B <- Li^H (conjugate transpose in place): V starts as Li^H so that V J = Li^H Y
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t / n, c = t % n;
+    if (c > i) {
+      C2 lo = B[c * n + i];
+      B[i * n + c] = cconj(lo);
+      B[c * n + i] = mk<R>(0, 0);
+    } else if (c == i) {
+      B[t] = cconj(B[t]);
+    }
+  }
+  __syncthreads();
+  jacobi<R>(A, B, n, 30, rc, rs, rp, rq, red, drop);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ev[i] = A[i * n + i].x;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int r = 0;
+    R vi = ev[i];
+    for (int j = 0; j < n; ++j) {
+      bool before;
+      if (drop[i] != drop[j]) before = drop[i] > drop[j];          // kept coordinates first
+      else before = (ev[j] < vi || (ev[j] == vi && j < i));
+      r += before ? 1 : 0;
+    }
+    perm[r] = i;
+  }
+  if (threadIdx.x == 0) {
+    int kept = 0;
+    for (int i = 0; i < n; ++i) kept += drop[i] ? 0 : 1;
+    cnt[0] = kept;
+  }
+  __syncthreads();
+  C2* ck = coef + (long long)k * n * m;
+  if (cnt[0] < m) {
+    // too few independent directions: keep the current block (identity on its first m coordinates)
+    for (int t = threadIdx.x; t < n * m; t += blockDim.x) {
+      int i = t / m, j = t % m;
+      ck[t] = (i == j) ? mk<R>(1, 0) : mk<R>(0, 0);
+    }
+    for (int j = threadIdx.x; j < m; j += blockDim.x) lam_out[(long long)k * m + j] = ga[j * n + j].x / go[j * n + j].x;
+    if (threadIdx.x == 0) set_status(status, PC_ENOCONV);
+    return;
+  }
+  for (int t = threadIdx.x; t < n * m; t += blockDim.x) {
+    int i = t / m, j = t % m;
+    ck[t] = cscale(B[i * n + perm[j]], D[i]);
+  }
+  for (int j = threadIdx.x; j < m; j += blockDim.x) lam_out[(long long)k * m + j] = ev[perm[j]];
+}
+
+template <typename R>
+int launch_small_rr(const typename cplx_t<R>::type* GA, const typename cplx_t<R>::type* GO, int n, int m, int nk,
+                    R drop_tol, const int* kdone, R* lam_out, typename cplx_t<R>::type* coef, int* status,
+                    cudaStream_t s) {
+  size_t sm = SmallSmem<R>::bytes(n);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_small_rr<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  if (sm > 200 * 1024) return PC_EINVAL;
+  k_small_rr<R><<<nk, 256, sm, s>>>(GA, GO, n, m, drop_tol, kdone, lam_out, coef, status);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+template int launch_small_rr<double>(const double2*, const double2*, int, int, int, double, const int*, double*, double2*, int*, cudaStream_t);
+template int launch_small_rr<float>(const float2*, const float2*, int, int, int, float, const int*, float*, float2*, int*, cudaStream_t);
+
+// Cholesky-QR transform: T = D Li^H with zero columns for dropped coordinates.
+template <typename R>
+__global__ __launch_bounds__(256) void k_small_chol(const typename cplx_t<R>::type* __restrict__ G, int m, R drop_tol,
+                                                    const typename cplx_t<R>::type* __restrict__ Gref, int rows_ref,
+                                                    R rel_tol, typename cplx_t<R>::type* __restrict__ T) {
+  typedef typename cplx_t<R>::type C2;
+  __shared__ C2 B[24 * 24];
+  __shared__ C2 tmp[24];
+  __shared__ R D[24];
+  __shared__ int drop[24];
+  const int k = blockIdx.x;
+  const C2* g = G + (long long)k * m * m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    R d = g[i * m + i].x;
+    bool keep = (d > (R)0 && d == d);
+    if (keep && Gref) {
+      R before = -Gref[(long long)k * rows_ref * m + (long long)(rows_ref - m + i) * m + i].x;
+      keep = d > rel_tol * before;
+    }
+    D[i] = keep ? (R)1 / sqrt(d) : (R)0;
+    drop[i] = 0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    int i = t / m, c = t % m;
+    C2 b1 = g[i * m + c], b2 = g[c * m + i];
+    R s = D[i] * D[c] * (R)0.5;
+    B[t] = mk<R>((b1.x + b2.x) * s, (b1.y - b2.y) * s);
+  }
+  __syncthreads();
+  chol_drop<R>(B, m, drop_tol, drop);
+  tri_inv_lower<R>(B, m, tmp);
+  C2* tk = T + (long long)k * m * m;
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    int i = t / m, c = t % m;
+    // T[i][c] = D_i conj(Li[c][i]); dropped columns vanish
+    C2 v = (c >= i && !drop[c]) ? cscale(cconj(B[c * m + i]), D[i]) : mk<R>(0, 0);
+    tk[t] = v;
+  }
+}
+template <typename R>
+int launch_small_chol(const typename cplx_t<R>::type* G, int m, int nk, R drop_tol,
+                      const typename cplx_t<R>::type* Gref, int rows_ref, R rel_tol, typename cplx_t<R>::type* T,
+                      cudaStream_t s) {
+  if (m > 24) return PC_EINVAL;
+  k_small_chol<R><<<nk, 256, 0, s>>>(G, m, drop_tol, Gref, rows_ref, rel_tol, T);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+template int launch_small_chol<double>(const double2*, int, int, double, const double2*, int, double, double2*, cudaStream_t);
+template int launch_small_chol<float>(const float2*, int, int, float, const float2*, int, float, float2*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Conjugate-direction coefficients in the small space.  With the Ritz coefficients cX
+// (cX^H GO cX = I) of the basis S = [X_old, W, P_old], the next conjugate block spans the
+// part of span(X_old) that is GO-orthogonal to the new Ritz block:
+//     Z = E - cX (cX^H GO E),  E = [I_m; 0],
+// orthonormalised in the GO metric (H = Z^H GO Z, Cholesky-QR; columns with H_jj below
+// abs_drop carry only rounding and are dropped).  span(X_new, P_new) = span(X_new, X_old),
+// and P_new = S cP is formed from GO-orthonormal coefficients, so no cancellation is
+// amplified in the tall update.  Locked k-points get cP = 0.
+template <typename R>
+__global__ __launch_bounds__(256) void k_small_pdir(const typename cplx_t<R>::type* __restrict__ GO,
+                                                    const typename cplx_t<R>::type* __restrict__ CX, int n, int m,
+                                                    const int* __restrict__ kdone, R abs_drop,
+                                                    typename cplx_t<R>::type* __restrict__ CP) {
+  typedef typename cplx_t<R>::type C2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  C2* cx = (C2*)smem;         // n*m
+  C2* z = cx + n * m;         // n*m
+  C2* gz = z + n * m;         // n*m
+  C2* Mm = gz + n * m;        // m*m  (also H, then T workspace)
+  C2* tmp = Mm + m * m;       // m
+  R* D = (R*)(tmp + m);       // m
+  int* drop = (int*)(D + m);  // m
+  const int k = blockIdx.x;
+  C2* cp = CP + (long long)k * n * m;
+  if (kdone && kdone[k]) {
+    for (int t = threadIdx.x; t < n * m; t += blockDim.x) cp[t] = mk<R>(0, 0);
+    return;
+  }
+  const C2* go = GO + (long long)k * n * n;
+  const C2* cxg = CX + (long long)k * n * m;
+  for (int t = threadIdx.x; t < n * m; t += blockDim.x) cx[t] = cxg[t];
+  __syncthreads();
+  // M = cX^H GO E  (GO symmetrised on the fly)
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    int i = t / m, j = t % m;
+    C2 s = mk<R>(0, 0);
+    for (int r = 0; r < n; ++r) {
+      C2 g1 = go[r * n + j], g2 = go[j * n + r];
+      C2 g = mk<R>((R)0.5 * (g1.x + g2.x), (R)0.5 * (g1.y - g2.y));
+      cfmac(s, cx[r * m + i], g);
+    }
+    Mm[t] = s;
+  }
+  __syncthreads();
+  // Z = E - cX M
+  for (int t = threadIdx.x; t < n * m; t += blockDim.x) {
+    int r = t / m, j = t % m;
+    C2 s = mk<R>((r == j) ? (R)1 : (R)0, 0);
+    for (int i = 0; i < m; ++i) {
+      C2 v = cmul(cx[r * m + i], Mm[i * m + j]);
+      s.x -= v.x; s.y -= v.y;
+    }
+    z[t] = s;
+  }
+  __syncthreads();
+  // GZ = GO Z
+  for (int t = threadIdx.x; t < n * m; t += blockDim.x) {
+    int r = t / m, j = t % m;
+    C2 s = mk<R>(0, 0);
+    for (int q = 0; q < n; ++q) {
+      C2 g1 = go[r * n + q], g2 = go[q * n + r];
+      C2 g = mk<R>((R)0.5 * (g1.x + g2.x), (R)0.5 * (g1.y - g2.y));
+      cfma(s, g, z[q * m + j]);
+    }
+    gz[t] = s;
+  }
+  __syncthreads();
+  // H = Z^H GZ, unit-diagonal scaled, dropped columns (H_jj <= abs_drop) decoupled
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    C2 s = mk<R>(0, 0);
+    for (int r = 0; r < n; ++r) cfmac(s, z[r * m + i], gz[r * m + i]);
+    D[i] = (s.x > abs_drop && s.x == s.x) ? (R)1 / sqrt(s.x) : (R)0;
+    drop[i] = 0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    int i = t / m, j = t % m;
+    C2 s1 = mk<R>(0, 0), s2 = mk<R>(0, 0);
+    for (int r = 0; r < n; ++r) { cfmac(s1, z[r * m + i], gz[r * m + j]); cfmac(s2, z[r * m + j], gz[r * m + i]); }
+    R sc = D[i] * D[j] * (R)0.5;
+    Mm[t] = mk<R>((s1.x + s2.x) * sc, (s1.y - s2.y) * sc);
+  }
+  __syncthreads();
+  chol_drop<R>(Mm, m, (R)1e-10, drop);
+  tri_inv_lower<R>(Mm, m, tmp);
+  // cP = Z T with T[i][c] = D_i conj(Li[c][i]) for c >= i and c kept
+  for (int t = threadIdx.x; t < n * m; t += blockDim.x) {
+    int r = t / m, c = t % m;
+    C2 s = mk<R>(0, 0);
+    if (!drop[c] && D[c] != (R)0) {
+      for (int i = 0; i <= c; ++i) {
+        C2 tv = cscale(cconj(Mm[c * m + i]), D[i]);
+        cfma(s, z[r * m + i], tv);
+      }
+    }
+    cp[t] = s;
+  }
+}
+
+template <typename R>
+int launch_small_pdir(const typename cplx_t<R>::type* GO, const typename cplx_t<R>::type* CX, int n, int m, int nk,
+                      const int* kdone, R abs_drop, typename cplx_t<R>::type* CP, cudaStream_t s) {
+  typedef typename cplx_t<R>::type C2;
+  if (m > 24 || n > 72) return PC_EINVAL;
+  size_t sm = sizeof(C2) * (3 * (size_t)n * m + (size_t)m * m + m) + sizeof(R) * m + sizeof(int) * m + 64;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_small_pdir<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_small_pdir<R><<<nk, 256, sm, s>>>(GO, CX, n, m, kdone, abs_drop, CP);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+template int launch_small_pdir<double>(const double2*, const double2*, int, int, int, const int*, double, double2*, cudaStream_t);
+template int launch_small_pdir<float>(const float2*, const float2*, int, int, int, const int*, float, float2*, cudaStream_t);

@@ -1,0 +1,838 @@
+// C ABI, context and host orchestration of the band + adjoint path.
+//
+// Per design (pc_set_design): SIMP interpolation, structure factors, Toeplitz operators
+// and the two inverse compliance operators (setup.cu).
+// Per band evaluation (pc_bands): a batched block preconditioned eigensolver over all
+// k at once (one independent projected problem per k), followed by one FP64
+// Rayleigh-Ritz step that also yields the FP64 stress coefficients for the adjoint.
+// PC_FP64 runs the block iteration in FP64; PC_MIXED runs it with FP32 vectors and
+// the split-BF16 tensor-core operator (gemm_tc.cu), then refines in FP64.
+// Per objective (pc_gap_and_grad): gap and weights, field synthesis and the weighted
+// per-voxel reduction (adjoint.cu).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+#include "kernels.h"
+#include "gemm_tc.h"
+
+extern int g_acc64;     // lobpcg.cu: FP64 accumulation switch (experiments)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct pc_ctx {
+  pc_params prm;
+  int N, M2, L, ne, m, nb;
+  int nk = 0;
+  double A[9], Tm[9], V, ve;
+  double lref, sO, sA, cA;  // lambda scale, Omega scale, operator scale, (2 pi)^2 V^2 / sA
+  Geom geom;
+  MaterialConsts mc;
+  PrecRef pr;
+  bool have_design = false, have_bands = false, have_grad = false;
+  int iterations = 0, unconv = 0;
+  double max_res = 0.0;
+  float ms_setup = 0.f, ms_bands = 0.f, ms_grad = 0.f;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int* h_unconv = nullptr;  // pinned
+  // per-design (FP64)
+  double *fields = nullptr, *dchi = nullptr, *chi = nullptr, *chi_mean = nullptr;
+  double2 *t1 = nullptr, *t2s = nullptr, *sfac = nullptr, *T = nullptr, *W = nullptr, *gj_row = nullptr, *gj_col = nullptr;
+  float2 *Wf = nullptr, *Tf = nullptr;  // scaled FP32 copies (mixed path)
+  int* status = nullptr;
+  // per k-set
+  double* Q = nullptr;
+  void* blk[15] = {nullptr};     // X AX OX W AW OW P AP OP Xn AXn OXn Pn APn OPn (R precision)
+  void *E = nullptr, *S = nullptr;  // strain / stress stacks (R precision)
+  void *gpart = nullptr, *GA = nullptr, *GO = nullptr, *Cc = nullptr, *Ct = nullptr;
+  void* lam = nullptr;           // nk*m (R)
+  double *rnorm = nullptr;
+  int *active = nullptr, *d_unconv = nullptr, *kdone = nullptr, *kdone_f = nullptr;
+  // FP64 Rayleigh-Ritz and adjoint
+  double2 *Xd = nullptr, *AXd = nullptr, *OXd = nullptr, *Ed = nullptr, *Sd = nullptr, *Th = nullptr, *St = nullptr;
+  double2 *gpartd = nullptr, *GAd = nullptr, *GOd = nullptr, *Cd = nullptr;
+  double *lamd = nullptr, *lam_nd = nullptr, *rnormd = nullptr;
+  int* actived = nullptr;
+  double *weights = nullptr;
+  int *pairs = nullptr, *npairs = nullptr;
+  double2* adj_t2 = nullptr;
+  TcPlan* tc = nullptr;
+  int debug = 0;  // PC_DEBUG=1 prints the residual history of the block iteration to stderr
+  unsigned long long seed = 0;  // PC_INIT_SEED: offset of the start-block perturbation
+  int small32 = 0;              // PC_SMALL_FP32=1: projected problems in FP32 (mixed form)
+  int apply64 = 0;              // PC_APPLY64=1: FP64 operator inside the mixed iteration (experiments)
+  double2 *sGA = nullptr, *sGO = nullptr, *sC = nullptr, *sCP = nullptr;  // FP64 widened projected problems
+  double* slam = nullptr;
+};
+
+static const char* kErr[] = {"PC_OK", "PC_EINVAL", "PC_EALIAS", "PC_ENOMEM", "PC_ECUDA",
+                             "PC_ESTATE", "PC_ENOCONV", "PC_EDOMAIN", "PC_ETIMEOUT"};
+
+extern "C" const char* pc_strerror(int code) {
+  if (code < 0 || code > 8) return "PC_UNKNOWN";
+  return kErr[code];
+}
+
+template <typename T> static int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return PC_ENOMEM;
+  }
+  return PC_OK;
+}
+template <typename T> static void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+static bool material_ok(const pc_material& m) {
+  return m.rho > 0 && m.E > 0 && m.nu > -1.0 && m.nu < 0.5 && std::isfinite(m.rho) && std::isfinite(m.E);
+}
+
+static void lattice_vectors(int lat, double a, double A[9]) {
+  // columns a_1, a_2, a_3; A[r*3+c] = component r of a_c
+  double P[3][3];
+  if (lat == PC_SC) {
+    double t[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    memcpy(P, t, sizeof(P));
+  } else if (lat == PC_BCC) {
+    double t[3][3] = {{-0.5, 0.5, 0.5}, {0.5, -0.5, 0.5}, {0.5, 0.5, -0.5}};  // rows: a_1, a_2, a_3
+    memcpy(P, t, sizeof(P));
+  } else {
+    double t[3][3] = {{0, 0.5, 0.5}, {0.5, 0, 0.5}, {0.5, 0.5, 0}};
+    memcpy(P, t, sizeof(P));
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) A[r * 3 + c] = a * P[c][r];
+}
+
+static double det3(const double m[9]) {
+  return m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) + m[2] * (m[3] * m[7] - m[4] * m[6]);
+}
+
+// T = A^{-T}: b_i . a_j = delta_ij, T row-major with K = T (Q + g)
+static void reciprocal(const double A[9], double T[9]) {
+  double d = det3(A);
+  double inv[9];
+  inv[0] = (A[4] * A[8] - A[5] * A[7]) / d;
+  inv[1] = (A[2] * A[7] - A[1] * A[8]) / d;
+  inv[2] = (A[1] * A[5] - A[2] * A[4]) / d;
+  inv[3] = (A[5] * A[6] - A[3] * A[8]) / d;
+  inv[4] = (A[0] * A[8] - A[2] * A[6]) / d;
+  inv[5] = (A[2] * A[3] - A[0] * A[5]) / d;
+  inv[6] = (A[3] * A[7] - A[4] * A[6]) / d;
+  inv[7] = (A[1] * A[6] - A[0] * A[7]) / d;
+  inv[8] = (A[0] * A[4] - A[1] * A[3]) / d;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) T[r * 3 + c] = inv[c * 3 + r];
+}
+
+static void lame(const pc_material& m, double* lam, double* mu) {
+  *mu = m.E / (2.0 * (1.0 + m.nu));
+  *lam = m.E * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu));
+}
+
+static void free_kset(pc_ctx* c) {
+  dfree(c->Q);
+  for (auto& b : c->blk) { if (b) cudaFree(b); b = nullptr; }
+  if (c->E) cudaFree(c->E); c->E = nullptr;
+  if (c->S) cudaFree(c->S); c->S = nullptr;
+  void** vs[] = {&c->gpart, &c->GA, &c->GO, &c->Cc, &c->Ct, &c->lam};
+  for (auto v : vs) { if (*v) cudaFree(*v); *v = nullptr; }
+  dfree(c->rnorm); dfree(c->active); dfree(c->d_unconv); dfree(c->kdone); dfree(c->kdone_f);
+  dfree(c->Xd); dfree(c->AXd); dfree(c->OXd); dfree(c->Ed); dfree(c->Sd); dfree(c->Th); dfree(c->St);
+  dfree(c->gpartd); dfree(c->GAd); dfree(c->GOd); dfree(c->Cd);
+  dfree(c->lamd); dfree(c->lam_nd); dfree(c->rnormd); dfree(c->actived);
+  dfree(c->weights); dfree(c->pairs); dfree(c->npairs); dfree(c->adj_t2);
+  dfree(c->sGA); dfree(c->sGO); dfree(c->sC); dfree(c->sCP); dfree(c->slam);
+  if (c->tc) { tc_plan_destroy(c->tc); c->tc = nullptr; }
+  c->nk = 0;
+  c->have_bands = false;
+  c->have_grad = false;
+}
+
+extern "C" void pc_destroy(pc_ctx* c) {
+  if (!c) return;
+  free_kset(c);
+  dfree(c->fields); dfree(c->dchi); dfree(c->chi); dfree(c->chi_mean);
+  dfree(c->t1); dfree(c->t2s); dfree(c->sfac); dfree(c->T); dfree(c->W); dfree(c->gj_row); dfree(c->gj_col);
+  dfree(c->Wf); dfree(c->Tf); dfree(c->status);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->h_unconv) cudaFreeHost(c->h_unconv);
+  delete c;
+}
+
+extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
+  if (!out) return PC_EINVAL;
+  *out = nullptr;
+  if (!p) return PC_EINVAL;
+  if (p->lattice < PC_SC || p->lattice > PC_FCC) return PC_EINVAL;
+  if (!(p->a > 0) || !std::isfinite(p->a)) return PC_EINVAL;
+  if (p->M < 1 || p->M > 5) return PC_EINVAL;
+  for (int i = 0; i < 3; ++i)
+    if (p->n[i] < 1 || p->n[i] > 256) return PC_EINVAL;
+  if (!material_ok(p->phase0) || !material_ok(p->phase1)) return PC_EINVAL;
+  if (!(p->penal >= 1.0) || !std::isfinite(p->penal)) return PC_EINVAL;
+  if (p->precision != PC_FP64 && p->precision != PC_MIXED) return PC_EINVAL;
+  if (p->tol < 0 || p->max_iter < 0) return PC_EINVAL;
+  const int M2 = 2 * p->M + 1;
+  const int N = M2 * M2 * M2;
+  if (p->nbands < 1 || p->nbands > 24 || p->nbands > N) return PC_EINVAL;
+  for (int i = 0; i < 3; ++i)
+    if (p->n[i] < M2) return PC_EALIAS;
+
+  pc_ctx* c = new (std::nothrow) pc_ctx();
+  if (!c) return PC_ENOMEM;
+  c->prm = *p;
+  {
+    const char* dbg = getenv("PC_DEBUG");
+    c->debug = (dbg && dbg[0] == '1') ? 1 : 0;
+    const char* acc = getenv("PC_ACC64");
+    
+    g_acc64 = (acc && acc[0] == '1') ? 1 : 0;
+    const char* a64 = getenv("PC_APPLY64");
+    c->apply64 = (a64 && a64[0] == '1') ? 1 : 0;
+    const char* s32 = getenv("PC_SMALL_FP32");
+    c->small32 = (s32 && s32[0] == '1') ? 1 : 0;
+    const char* sd = getenv("PC_INIT_SEED");
+    c->seed = sd ? strtoull(sd, nullptr, 10) : 0ull;
+
+  }
+  if (c->prm.tol == 0) c->prm.tol = (p->precision == PC_FP64) ? 1e-9 : 1e-4;
+  if (c->prm.max_iter == 0) c->prm.max_iter = (p->precision == PC_FP64) ? 200 : 120;
+  c->M2 = M2;
+  c->N = N;
+  c->L = 4 * p->M + 1;
+  c->ne = p->n[0] * p->n[1] * p->n[2];
+  c->nb = p->nbands;
+  c->m = std::min(std::min(p->nbands + 4, 24), N);
+  lattice_vectors(p->lattice, p->a, c->A);
+  reciprocal(c->A, c->Tm);
+  c->V = std::fabs(det3(c->A));
+  c->ve = c->V / c->ne;
+  const double two_pi = 2.0 * M_PI;
+  c->lref = two_pi * two_pi * p->phase1.E / (p->phase1.rho * p->a * p->a);
+  c->sO = c->V * p->phase1.rho;
+  c->sA = c->lref * c->sO;
+  c->cA = two_pi * two_pi * c->V * c->V / c->sA;
+  memcpy(c->geom.T, c->Tm, sizeof(c->Tm));
+  c->geom.M = p->M;
+  c->geom.N = N;
+  c->mc.penal = p->penal;
+  c->mc.rho0 = p->phase0.rho;
+  c->mc.rho1 = p->phase1.rho;
+  c->mc.f1_0 = (1.0 - 2.0 * p->phase0.nu) / p->phase0.E;
+  c->mc.f1_1 = (1.0 - 2.0 * p->phase1.nu) / p->phase1.E;
+  c->mc.f2_0 = (1.0 + p->phase0.nu) / p->phase0.E;
+  c->mc.f2_1 = (1.0 + p->phase1.nu) / p->phase1.E;
+  lame(p->phase0, &c->pr.lam0, &c->pr.mu0);
+  lame(p->phase1, &c->pr.lam1, &c->pr.mu1);
+  c->pr.rho0 = p->phase0.rho;
+  c->pr.rho1 = p->phase1.rho;
+  c->pr.two_pi_sq_V_over_sA = two_pi * two_pi * c->V / c->sA;
+  c->pr.half_lref_V_over_sA = 0.5 * c->lref * c->V / c->sA;
+
+  const size_t NN = (size_t)N * N;
+  const size_t ne = c->ne, L = c->L;
+  int rc = PC_OK;
+  rc |= dalloc(&c->fields, 3 * ne);
+  rc |= dalloc(&c->dchi, ne);
+  rc |= dalloc(&c->chi, ne);
+  rc |= dalloc(&c->chi_mean, 1);
+  rc |= dalloc(&c->t1, 3 * (size_t)p->n[0] * p->n[1] * L);
+  rc |= dalloc(&c->t2s, 3 * (size_t)p->n[0] * L * L);
+  rc |= dalloc(&c->sfac, 3 * L * L * L);
+  rc |= dalloc(&c->T, 3 * NN);
+  rc |= dalloc(&c->W, 2 * NN);
+  rc |= dalloc(&c->gj_row, 4 * (size_t)N);
+  rc |= dalloc(&c->gj_col, 4 * (size_t)N);
+  rc |= dalloc(&c->status, 1);
+  if (p->precision == PC_MIXED) {
+    rc |= dalloc(&c->Wf, 2 * NN);
+    rc |= dalloc(&c->Tf, NN);
+  }
+  if (rc != PC_OK) { pc_destroy(c); return PC_ENOMEM; }
+  if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
+      cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+      cudaMallocHost((void**)&c->h_unconv, sizeof(int)) != cudaSuccess) {
+    pc_destroy(c);
+    return PC_ECUDA;
+  }
+  *out = c;
+  return PC_OK;
+}
+
+extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
+  if (!c || !q || nk < 1 || nk > 100000) return PC_EINVAL;
+  free_kset(c);
+  const int m = c->m, N = c->N, n3 = 3 * N;
+  const size_t nvec = (size_t)nk * m;
+  const size_t esz = (c->prm.precision == PC_FP64) ? sizeof(double2) : sizeof(float2);
+  const size_t rsz = (c->prm.precision == PC_FP64) ? sizeof(double) : sizeof(float);
+  int rc = PC_OK;
+  rc |= dalloc(&c->Q, 3 * (size_t)nk);
+  for (auto& b : c->blk)
+    if (cudaMalloc(&b, nvec * n3 * esz) != cudaSuccess) { b = nullptr; rc = PC_ENOMEM; }
+  if (cudaMalloc(&c->E, 6 * nvec * N * esz) != cudaSuccess) { c->E = nullptr; rc = PC_ENOMEM; }
+  if (cudaMalloc(&c->S, 6 * nvec * N * esz) != cudaSuccess) { c->S = nullptr; rc = PC_ENOMEM; }
+  const size_t g = (size_t)nk * 72 * 72;
+  if (cudaMalloc(&c->gpart, 8 * g * esz) != cudaSuccess) { c->gpart = nullptr; rc = PC_ENOMEM; }
+  if (cudaMalloc(&c->GA, g * esz) != cudaSuccess) { c->GA = nullptr; rc = PC_ENOMEM; }
+  if (cudaMalloc(&c->GO, g * esz) != cudaSuccess) { c->GO = nullptr; rc = PC_ENOMEM; }
+  if (cudaMalloc(&c->Cc, g * esz) != cudaSuccess) { c->Cc = nullptr; rc = PC_ENOMEM; }
+  if (cudaMalloc(&c->Ct, g * esz) != cudaSuccess) { c->Ct = nullptr; rc = PC_ENOMEM; }
+  if (cudaMalloc(&c->lam, nvec * rsz) != cudaSuccess) { c->lam = nullptr; rc = PC_ENOMEM; }
+  rc |= dalloc(&c->rnorm, nvec);
+  rc |= dalloc(&c->active, nvec);
+  rc |= dalloc(&c->d_unconv, 1);
+  rc |= dalloc(&c->kdone, (size_t)nk);
+  rc |= dalloc(&c->kdone_f, (size_t)nk);
+  rc |= dalloc(&c->Xd, nvec * n3);
+  rc |= dalloc(&c->AXd, nvec * n3);
+  rc |= dalloc(&c->OXd, nvec * n3);
+  rc |= dalloc(&c->Th, nvec * n3);
+  rc |= dalloc(&c->Ed, 6 * nvec * N);
+  rc |= dalloc(&c->Sd, 6 * nvec * N);
+  rc |= dalloc(&c->St, 6 * nvec * N);
+  rc |= dalloc(&c->gpartd, 8 * (size_t)nk * m * m);
+  rc |= dalloc(&c->GAd, (size_t)nk * m * m);
+  rc |= dalloc(&c->GOd, (size_t)nk * m * m);
+  rc |= dalloc(&c->Cd, (size_t)nk * m * m);
+  rc |= dalloc(&c->lamd, nvec);
+  rc |= dalloc(&c->lam_nd, (size_t)nk * c->nb);
+  rc |= dalloc(&c->rnormd, nvec);
+  rc |= dalloc(&c->actived, nvec);
+  rc |= dalloc(&c->weights, (size_t)nk * c->nb);
+  rc |= dalloc(&c->pairs, (size_t)nk * c->nb);
+  rc |= dalloc(&c->npairs, 1);
+  rc |= dalloc(&c->sGA, g);
+  rc |= dalloc(&c->sGO, g);
+  rc |= dalloc(&c->sC, g);
+  rc |= dalloc(&c->sCP, g);
+  rc |= dalloc(&c->slam, nvec);
+  rc |= dalloc(&c->adj_t2, (size_t)nk * c->nb * 9 * c->M2 * c->prm.n[1] * c->prm.n[2]);
+  if (rc == PC_OK && c->prm.precision == PC_MIXED) {
+    c->tc = tc_plan_create(N, (int)nvec);
+    if (!c->tc) rc = PC_ENOMEM;
+  }
+  if (rc != PC_OK) { free_kset(c); return PC_ENOMEM; }
+  if (cudaMemcpy(c->Q, q, 3 * sizeof(double) * nk, cudaMemcpyHostToDevice) != cudaSuccess) {
+    free_kset(c);
+    return PC_ECUDA;
+  }
+  c->nk = nk;
+  return PC_OK;
+}
+
+extern "C" int pc_set_design(pc_ctx* c, const double* rho, void* stream) {
+  if (!c || !rho) return PC_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  PC_CUDA_TRY(cudaEventRecord(c->ev0, s));
+  SetupArgs a;
+  a.rho = rho;
+  a.n0 = c->prm.n[0]; a.n1 = c->prm.n[1]; a.n2 = c->prm.n[2];
+  a.M = c->prm.M;
+  a.V = c->V;
+  a.mc = c->mc;
+  a.fields = c->fields; a.dchi = c->dchi; a.chi = c->chi; a.chi_mean = c->chi_mean;
+  a.t1 = c->t1; a.t2 = c->t2s; a.sfac = c->sfac; a.T = c->T; a.W = c->W;
+  a.gj_row = c->gj_row; a.gj_col = c->gj_col;
+  a.status = c->status;
+  int rc = launch_setup(a, s);
+  if (rc) return rc;
+  if (c->prm.precision == PC_MIXED) {
+    const long long NN = (long long)c->N * c->N;
+    // scaled FP32 operators: W * (2 pi)^2 V^2 / sA and T_rho / sO are O(1)
+    rc = launch_d2f(c->W, c->Wf, 2 * NN, c->cA, s);
+    if (rc) return rc;
+    rc = launch_d2f(c->T, c->Tf, NN, 1.0 / c->sO, s);
+    if (rc) return rc;
+    rc = tc_prepare_operators(c->tc, c->W, c->T, c->cA, 1.0 / c->sO, s);
+    if (rc) return rc;
+  }
+  PC_CUDA_TRY(cudaEventRecord(c->ev1, s));
+  c->have_design = true;
+  c->have_bands = false;
+  c->have_grad = false;
+  return PC_OK;
+}
+
+// ---------------------------------------------------------------------------
+template <typename R> struct Ops;
+// drop_small: pivot below which a unit-scaled Gram column counts as dependent.
+// rel_drop: a new direction whose Omega-norm^2 after projection is below this fraction of
+// its norm^2 before carries mostly rounding noise and is dropped.
+template <> struct Ops<double> {
+  typedef double2 C2;
+  static constexpr double drop_small = 1e-12;
+  static constexpr double rel_drop = 1e-10;
+};
+template <> struct Ops<float> {
+  typedef float2 C2;
+  static constexpr float drop_small = 1e-5f;
+  static constexpr float rel_drop = 1e-4f;
+};
+
+// A x and Omega x for nvec vectors with the per-k geometry Q (vector v belongs to k = v / m).
+static int apply_fp64(pc_ctx* c, const double2* X, double2* AX, double2* OX, int nvec, int m, const double* Q,
+                      double epi, double alpha_omega, double2* E, double2* S, cudaStream_t s) {
+  const int N = c->N;
+  const long long NN = (long long)N * N;
+  int rc = launch_strain<double>(X, nvec, m, c->geom, Q, E, s);
+  if (rc) return rc;
+  rc = launch_gemm<double>(N, nvec, N, c->W, N, E, N, S, N, 1.0, s);
+  if (rc) return rc;
+  rc = launch_gemm<double>(N, 5 * nvec, N, c->W + NN, N, E + (long long)nvec * N, N, S + (long long)nvec * N, N, 1.0, s);
+  if (rc) return rc;
+  rc = launch_epilogue<double>(S, nvec, m, c->geom, Q, epi, epi, AX, s);
+  if (rc) return rc;
+  return launch_gemm<double>(N, 3 * nvec, N, c->T, N, X, N, OX, N, alpha_omega, s);
+}
+
+static int apply_fp32(pc_ctx* c, const float2* X, float2* AX, float2* OX, int nvec, int m, cudaStream_t s) {
+  if (c->apply64) {  // experiment switch: FP64 operator on widened FP32 vectors
+    const long long n = (long long)nvec * 3 * c->N;
+    int rc = launch_convert_f2d(X, c->Xd, n, s);
+    if (!rc) rc = apply_fp64(c, c->Xd, c->AXd, c->OXd, nvec, m, c->Q, c->cA, 1.0 / c->sO, c->Ed, c->Sd, s);
+    if (!rc) rc = launch_d2f(c->AXd, AX, n, 1.0, s);
+    if (!rc) rc = launch_d2f(c->OXd, OX, n, 1.0, s);
+    return rc;
+  }
+  if (c->tc && tc_available(c->tc)) return tc_apply(c->tc, X, AX, OX, nvec, m, c->geom, c->Q, s);
+  const int N = c->N;
+  const long long NN = (long long)N * N;
+  float2* E = (float2*)c->E;
+  float2* S = (float2*)c->S;
+  int rc = launch_strain<float>(X, nvec, m, c->geom, c->Q, E, s);
+  if (rc) return rc;
+  rc = launch_gemm<float>(N, nvec, N, c->Wf, N, E, N, S, N, 1.0f, s);
+  if (rc) return rc;
+  rc = launch_gemm<float>(N, 5 * nvec, N, c->Wf + NN, N, E + (long long)nvec * N, N, S + (long long)nvec * N, N, 1.0f, s);
+  if (rc) return rc;
+  rc = launch_epilogue<float>(S, nvec, m, c->geom, c->Q, 1.0f, 1.0f, AX, s);
+  if (rc) return rc;
+  return launch_gemm<float>(N, 3 * nvec, N, c->Tf, N, X, N, OX, N, 1.0f, s);
+}
+
+template <typename R>
+static int apply_R(pc_ctx* c, const typename Ops<R>::C2* X, typename Ops<R>::C2* AX, typename Ops<R>::C2* OX, cudaStream_t s);
+template <>
+int apply_R<double>(pc_ctx* c, const double2* X, double2* AX, double2* OX, cudaStream_t s) {
+  return apply_fp64(c, X, AX, OX, c->nk * c->m, c->m, c->Q, c->cA, 1.0 / c->sO, (double2*)c->E, (double2*)c->S, s);
+}
+template <>
+int apply_R<float>(pc_ctx* c, const float2* X, float2* AX, float2* OX, cudaStream_t s) {
+  return apply_fp32(c, X, AX, OX, c->nk * c->m, c->m, s);
+}
+
+template <typename R>
+static UpdateArgs<R> upd(pc_ctx* c, int nblk, int identity_last, const void* Cmat, long long cstride, int cld, int mout) {
+  UpdateArgs<R> u;
+  memset(&u, 0, sizeof(u));
+  u.nblk = nblk;
+  u.identity_last = identity_last;
+  u.C = (const typename cplx_t<R>::type*)Cmat;
+  u.cstride = cstride;
+  u.cld = cld;
+  u.m = c->m;
+  u.mout = mout;
+  u.n3 = 3 * c->N;
+  u.nk = c->nk;
+  u.in_kstride = (long long)c->m * 3 * c->N;
+  u.out_kstride = (long long)mout * 3 * c->N;
+  u.ntrip = 3;
+  return u;
+}
+
+static const int kRefresh = 10;
+
+// The projected problems (Rayleigh-Ritz pencil, conjugate-direction coefficients and the
+// Cholesky-QR of the search directions) run in FP64 for both precisions: in the mixed form
+// their FP32 Gram inputs are widened, solved in FP64 and the coefficients narrowed again.
+// PC_SMALL_FP32=1 keeps them in FP32 (for experiments).
+template <typename R> struct SmallTol;
+template <> struct SmallTol<double> { static constexpr double pdir_abs = 1e-26; };
+template <> struct SmallTol<float> { static constexpr double pdir_abs = 1e-12; };
+
+template <typename R>
+static int small_rr_any(pc_ctx* c, const typename Ops<R>::C2* GA, const typename Ops<R>::C2* GO, int n, int m,
+                        const int* kdone, R* lam, typename Ops<R>::C2* cX, typename Ops<R>::C2* cP, cudaStream_t s);
+template <>
+int small_rr_any<double>(pc_ctx* c, const double2* GA, const double2* GO, int n, int m, const int* kdone, double* lam,
+                         double2* cX, double2* cP, cudaStream_t s) {
+  int rc = launch_small_rr<double>(GA, GO, n, m, c->nk, Ops<double>::drop_small, kdone, lam, cX, c->status, s);
+  if (!rc && cP) rc = launch_small_pdir<double>(GO, cX, n, m, c->nk, kdone, SmallTol<double>::pdir_abs, cP, s);
+  return rc;
+}
+template <>
+int small_rr_any<float>(pc_ctx* c, const float2* GA, const float2* GO, int n, int m, const int* kdone, float* lam,
+                        float2* cX, float2* cP, cudaStream_t s) {
+  if (c->small32) {
+    int rc = launch_small_rr<float>(GA, GO, n, m, c->nk, Ops<float>::drop_small, kdone, lam, cX, c->status, s);
+    if (!rc && cP) rc = launch_small_pdir<float>(GO, cX, n, m, c->nk, kdone, (float)SmallTol<float>::pdir_abs, cP, s);
+    return rc;
+  }
+  const long long nn = (long long)c->nk * n * n;
+  int rc = launch_convert_f2d(GA, c->sGA, nn, s);
+  if (!rc) rc = launch_convert_f2d(GO, c->sGO, nn, s);
+  if (!rc) rc = launch_real_f2d(lam, c->slam, (long long)c->nk * m, s);
+  if (!rc) rc = launch_small_rr<double>(c->sGA, c->sGO, n, m, c->nk, (double)Ops<float>::drop_small, kdone, c->slam,
+                                        c->sC, c->status, s);
+  if (!rc && cP) rc = launch_small_pdir<double>(c->sGO, c->sC, n, m, c->nk, kdone, SmallTol<float>::pdir_abs, c->sCP, s);
+  if (!rc) rc = launch_d2f(c->sC, cX, (long long)c->nk * n * m, 1.0, s);
+  if (!rc && cP) rc = launch_d2f(c->sCP, cP, (long long)c->nk * n * m, 1.0, s);
+  if (!rc) rc = launch_real_d2f(c->slam, lam, (long long)c->nk * m, s);
+  return rc;
+}
+template <typename R>
+static int small_chol_any(pc_ctx* c, const typename Ops<R>::C2* G, int m, typename Ops<R>::C2* T, cudaStream_t s);
+template <>
+int small_chol_any<double>(pc_ctx* c, const double2* G, int m, double2* T, cudaStream_t s) {
+  return launch_small_chol<double>(G, m, c->nk, Ops<double>::drop_small, nullptr, 0, 0.0, T, s);
+}
+template <>
+int small_chol_any<float>(pc_ctx* c, const float2* G, int m, float2* T, cudaStream_t s) {
+  if (c->small32) return launch_small_chol<float>(G, m, c->nk, Ops<float>::drop_small, nullptr, 0, 0.0f, T, s);
+  int rc = launch_convert_f2d(G, c->sGO, (long long)c->nk * m * m, s);
+  if (!rc) rc = launch_small_chol<double>(c->sGO, m, c->nk, (double)Ops<float>::drop_small, nullptr, 0, 0.0, c->sC, s);
+  if (!rc) rc = launch_d2f(c->sC, T, (long long)c->nk * m * m, 1.0, s);
+  return rc;
+}
+
+// The batched block iteration (all k at once).  Per iteration and k:
+//   R = A X - Omega X Lambda,  W = P(R) on the unconverged columns;
+//   W <- W - X (OX^H W) - P (OP^H W); AW, OW = A W, Omega W (explicit products);
+//   W <- W T (Cholesky-QR in the Omega metric, dependent directions dropped);
+//   Rayleigh-Ritz on S = [X W P]: X <- S cX, P <- S cP (cP from the small space).
+// k-points whose wanted bands are all converged are locked.
+template <typename R>
+static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
+  typedef typename Ops<R>::C2 C2;
+  const int m = c->m, nk = c->nk, n3 = 3 * c->N, nb = c->nb;
+  C2* b[15];
+  for (int i = 0; i < 15; ++i) b[i] = (C2*)c->blk[i];
+  C2 *X = b[0], *AX = b[1], *OX = b[2], *Wb = b[3], *AW = b[4], *OW = b[5], *P = b[6], *AP = b[7], *OP = b[8];
+  C2 *Xn = b[9], *AXn = b[10], *OXn = b[11], *Pn = b[12], *APn = b[13], *OPn = b[14];
+  C2* part = (C2*)c->gpart;
+  C2 *GA = (C2*)c->GA, *GO = (C2*)c->GO, *Cc = (C2*)c->Cc, *Ct = (C2*)c->Ct;
+  R* lam = (R*)c->lam;
+  int rc;
+#define TRY(x) do { rc = (x); if (rc) return rc; } while (0)
+  PC_CUDA_TRY(cudaMemsetAsync(c->kdone, 0, sizeof(int) * nk, s));
+  TRY(launch_init_guess<R>(X, nk, m, c->geom, c->Q, c->seed, s));
+  TRY(apply_R<R>(c, X, AX, OX, s));
+  {
+    BlockList<R> A1 = {{X, nullptr, nullptr}}, B1 = {{AX, nullptr, nullptr}}, B2 = {{OX, nullptr, nullptr}};
+    TRY(launch_gram<R>(A1, 1, B1, 1, nk, m, n3, (R)1, part, GA, s));
+    TRY(launch_gram<R>(A1, 1, B2, 1, nk, m, n3, (R)1, part, GO, s));
+    TRY(small_rr_any<R>(c, GA, GO, m, m, c->kdone, lam, Cc, nullptr, s));
+    UpdateArgs<R> u = upd<R>(c, 1, 0, Cc, (long long)m * m, m, m);
+    u.in[0][0] = X; u.in[1][0] = AX; u.in[2][0] = OX;
+    u.out[0] = Xn; u.out[1] = AXn; u.out[2] = OXn;
+    TRY(launch_update<R>(u, s));
+    std::swap(X, Xn); std::swap(AX, AXn); std::swap(OX, OXn);
+  }
+  bool hasP = false;
+  int it = 0;
+  c->unconv = nk;
+  for (it = 0; it < c->prm.max_iter; ++it) {
+    // The products A X and Omega X are carried along by the same linear combinations as X;
+    // their rounding drifts away from the true products.  Every kRefresh iterations they
+    // are recomputed from X and the conjugate block is restarted.
+    if (it > 0 && it % kRefresh == 0) {
+      TRY(apply_R<R>(c, X, AX, OX, s));
+      hasP = false;
+    }
+    TRY(launch_resnorm<R>(AX, OX, lam, nk, m, nb, n3, c->prm.tol, c->rnorm, c->active, c->kdone, c->d_unconv, s));
+    PC_CUDA_TRY(cudaMemcpyAsync(c->h_unconv, c->d_unconv, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PC_CUDA_TRY(cudaStreamSynchronize(s));
+    c->unconv = *c->h_unconv;
+    if (c->debug) {
+      const int nv = nk * m;
+      std::vector<double> h(nv);
+      cudaMemcpy(h.data(), c->rnorm, sizeof(double) * nv, cudaMemcpyDeviceToHost);
+      double mx = 0;
+      int kmx = 0;
+      for (int k = 0; k < nk; ++k)
+        for (int j = 0; j < nb; ++j)
+          if (h[k * m + j] > mx) { mx = h[k * m + j]; kmx = k; }
+      fprintf(stderr, "[pc] it %d unconverged_k %d max_res %.3e at k %d\n", it, c->unconv, mx, kmx);
+      const char* dk = getenv("PC_DEBUG_K");
+      if (dk) {
+        int kk = atoi(dk);
+        fprintf(stderr, "[pc]   k %d col res:", kk);
+        for (int j = 0; j < m; ++j) fprintf(stderr, " %.1e", h[kk * m + j]);
+        fprintf(stderr, "\n");
+      }
+    }
+    if (c->unconv == 0) break;
+    TRY(launch_precond<R>(AX, OX, lam, c->active, c->kdone, nk, m, nb, c->geom, c->Q, c->pr, c->chi_mean, Wb, s));
+    // W <- W - X (OX^H W) - P (OP^H W), before the operator is applied
+    {
+      const int nproj = hasP ? 2 : 1;
+      BlockList<R> A1 = {{OX, OP, nullptr}}, B1 = {{Wb, nullptr, nullptr}};
+      TRY(launch_gram<R>(A1, nproj, B1, 1, nk, m, n3, (R)-1, part, Ct, s));
+      UpdateArgs<R> u = upd<R>(c, nproj + 1, 1, Ct, (long long)nproj * m * m, m, m);
+      u.ntrip = 1;
+      u.in[0][0] = X;
+      if (hasP) { u.in[0][1] = P; u.in[0][2] = Wb; } else { u.in[0][1] = Wb; }
+      u.out[0] = Wb;
+      TRY(launch_update<R>(u, s));
+    }
+    TRY(apply_R<R>(c, Wb, AW, OW, s));
+    // W <- W T with T^H (W^H Omega W) T = I, dependent directions dropped
+    {
+      BlockList<R> A1 = {{Wb, nullptr, nullptr}}, B1 = {{OW, nullptr, nullptr}};
+      TRY(launch_gram<R>(A1, 1, B1, 1, nk, m, n3, (R)1, part, GO, s));
+      TRY(small_chol_any<R>(c, GO, m, Cc, s));
+      UpdateArgs<R> u = upd<R>(c, 1, 0, Cc, (long long)m * m, m, m);
+      u.in[0][0] = Wb; u.in[1][0] = AW; u.in[2][0] = OW;
+      u.out[0] = Wb; u.out[1] = AW; u.out[2] = OW;
+      TRY(launch_update<R>(u, s));
+    }
+    // Rayleigh-Ritz on S = [X W P]
+    const int ns = hasP ? 3 : 2;
+    const int n = ns * m;
+    BlockList<R> S1 = {{X, Wb, P}}, SA = {{AX, AW, AP}}, SO = {{OX, OW, OP}};
+    TRY(launch_gram<R>(S1, ns, SA, ns, nk, m, n3, (R)1, part, GA, s));
+    TRY(launch_gram<R>(S1, ns, SO, ns, nk, m, n3, (R)1, part, GO, s));
+    TRY(small_rr_any<R>(c, GA, GO, n, m, c->kdone, lam, Cc, Ct, s));
+    {
+      UpdateArgs<R> u = upd<R>(c, ns, 0, Cc, (long long)n * m, m, m);
+      u.in[0][0] = X; u.in[0][1] = Wb; u.in[0][2] = P;
+      u.in[1][0] = AX; u.in[1][1] = AW; u.in[1][2] = AP;
+      u.in[2][0] = OX; u.in[2][1] = OW; u.in[2][2] = OP;
+      u.out[0] = Xn; u.out[1] = AXn; u.out[2] = OXn;
+      TRY(launch_update<R>(u, s));
+      UpdateArgs<R> v = u;
+      v.C = Ct;
+      v.out[0] = Pn; v.out[1] = APn; v.out[2] = OPn;
+      TRY(launch_update<R>(v, s));
+    }
+    std::swap(X, Xn); std::swap(AX, AXn); std::swap(OX, OXn);
+    std::swap(P, Pn); std::swap(AP, APn); std::swap(OP, OPn);
+    hasP = true;
+  }
+  c->iterations = it;
+  // keep the final block where the FP64 step looks for it
+  C2* order[15] = {X, AX, OX, Wb, AW, OW, P, AP, OP, Xn, AXn, OXn, Pn, APn, OPn};
+  for (int i = 0; i < 15; ++i) c->blk[i] = order[i];
+#undef TRY
+  return PC_OK;
+}
+
+// One FP64 Rayleigh-Ritz step on the final block: FP64 operator, FP64 Gram matrices,
+// FP64 projected eigenproblem; yields lambda, theta and the stresses of theta.
+static int fp64_rayleigh_ritz(pc_ctx* c, cudaStream_t s) {
+  const int m = c->m, nk = c->nk, N = c->N, n3 = 3 * N;
+  const long long nvec = (long long)nk * m;
+  int rc;
+  const double2* X;
+  if (c->prm.precision == PC_MIXED) {
+    rc = launch_convert_f2d((const float2*)c->blk[0], c->Xd, nvec * n3, s);
+    if (rc) return rc;
+    X = c->Xd;
+  } else {
+    X = (const double2*)c->blk[0];
+  }
+  rc = apply_fp64(c, X, c->AXd, c->OXd, (int)nvec, m, c->Q, c->cA, 1.0 / c->sO, c->Ed, c->Sd, s);
+  if (rc) return rc;
+  BlockList<double> A1 = {{X, nullptr, nullptr}}, B1 = {{c->AXd, nullptr, nullptr}}, B2 = {{c->OXd, nullptr, nullptr}};
+  rc = launch_gram<double>(A1, 1, B1, 1, nk, m, n3, 1.0, c->gpartd, c->GAd, s);
+  if (rc) return rc;
+  rc = launch_gram<double>(A1, 1, B2, 1, nk, m, n3, 1.0, c->gpartd, c->GOd, s);
+  if (rc) return rc;
+  rc = launch_small_rr<double>(c->GAd, c->GOd, m, m, nk, 1e-12, nullptr, c->lamd, c->Cd, c->status, s);
+  if (rc) return rc;
+  // theta = X C; A theta and Omega theta for the residual report
+  UpdateArgs<double> u = upd<double>(c, 1, 0, c->Cd, (long long)m * m, m, m);
+  u.in[0][0] = X; u.in[1][0] = c->AXd; u.in[2][0] = c->OXd;
+  // the strain stacks Ed (6 nvec N = 2 nvec 3N entries) are free after the apply: they take
+  // A theta and Omega theta for the residual report
+  double2* Ath = c->Ed;
+  double2* Oth = c->Ed + nvec * n3;
+  u.out[0] = c->Th;
+  u.out[1] = Ath;
+  u.out[2] = Oth;
+  rc = launch_update<double>(u, s);
+  if (rc) return rc;
+  PC_CUDA_TRY(cudaMemsetAsync(c->kdone_f, 0, sizeof(int) * nk, s));
+  rc = launch_resnorm<double>(Ath, Oth, c->lamd, nk, m, c->nb, n3, c->prm.tol, c->rnormd, c->actived,
+                              c->kdone_f, c->d_unconv, s);
+  if (rc) return rc;
+  // stresses of theta: St[s] = Sd[s] C
+  for (int half = 0; half < 2; ++half) {
+    UpdateArgs<double> v = upd<double>(c, 1, 0, c->Cd, (long long)m * m, m, m);
+    v.n3 = N;
+    v.in_kstride = (long long)m * N;
+    v.out_kstride = (long long)m * N;
+    for (int t = 0; t < 3; ++t) {
+      int sidx = half * 3 + t;
+      v.in[t][0] = c->Sd + (long long)sidx * nvec * N;
+      v.out[t] = c->St + (long long)sidx * nvec * N;
+    }
+    rc = launch_update<double>(v, s);
+    if (rc) return rc;
+  }
+  return PC_OK;
+}
+
+extern "C" int pc_bands(pc_ctx* c, double* omega, void* stream) {
+  if (!c || !omega) return PC_EINVAL;
+  if (!c->have_design || c->nk == 0) return PC_ESTATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  PC_CUDA_TRY(cudaEventRecord(c->ev0, s));
+  int rc = (c->prm.precision == PC_FP64) ? run_block_iteration<double>(c, s) : run_block_iteration<float>(c, s);
+  if (rc) return rc;
+  rc = fp64_rayleigh_ritz(c, s);
+  if (rc) return rc;
+  rc = launch_omega(c->lamd, c->nk, c->nb, c->m, c->lref, omega, c->lam_nd, s);
+  if (rc) return rc;
+  PC_CUDA_TRY(cudaEventRecord(c->ev1, s));
+  c->have_bands = true;
+  c->have_grad = false;
+  return PC_OK;
+}
+
+extern "C" int pc_gap_and_grad(pc_ctx* c, int n_lower, int mode, const double* w, double* gap, double* grad,
+                               void* stream) {
+  if (!c || !gap) return PC_EINVAL;
+  if (mode != PC_GAP_OMEGA && mode != PC_GAP_LAMBDA && mode != PC_GRAD_ALLBANDS) return PC_EINVAL;
+  if (mode == PC_GRAD_ALLBANDS && !w) return PC_EINVAL;
+  if (mode != PC_GRAD_ALLBANDS && (n_lower < 1 || n_lower >= c->nb)) return PC_EINVAL;
+  if (!c->have_bands) return PC_ESTATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  PC_CUDA_TRY(cudaEventRecord(c->ev0, s));
+  GapArgs g;
+  g.lam = c->lam_nd;
+  g.nk = c->nk; g.nb = c->nb; g.n_lower = n_lower; g.mode = mode;
+  g.lref = c->lref;
+  g.rel_tol = 1e-8;
+  g.w_user = w;
+  g.gap_out = gap;
+  g.weights = c->weights;
+  g.pairs = c->pairs;
+  g.npairs = c->npairs;
+  int rc = launch_gap(g, s);
+  if (rc) return rc;
+  if (grad) {
+    AdjointArgs a;
+    a.theta = c->Th;
+    a.sig = c->St;
+    a.lam = c->lam_nd;
+    a.weights = c->weights;
+    a.pairs = c->pairs;
+    a.npairs = c->npairs;
+    a.max_pairs = c->nk * c->nb;
+    a.nk = c->nk; a.nb = c->nb; a.m = c->m; a.N = c->N; a.M = c->prm.M;
+    a.n0 = c->prm.n[0]; a.n1 = c->prm.n[1]; a.n2 = c->prm.n[2];
+    a.lref = c->lref;
+    a.inv_sO = 1.0 / c->sO;
+    a.d_rho = c->mc.rho1 - c->mc.rho0;
+    a.d_f1 = c->mc.f1_1 - c->mc.f1_0;
+    a.d_f2 = c->mc.f2_1 - c->mc.f2_0;
+    a.two_pi_V_sq = (2.0 * M_PI * c->V) * (2.0 * M_PI * c->V);
+    a.ve = c->ve;
+    a.dchi = c->dchi;
+    a.t2 = c->adj_t2;
+    a.grad = grad;
+    rc = launch_adjoint(a, s);
+    if (rc) return rc;
+  }
+  PC_CUDA_TRY(cudaEventRecord(c->ev1, s));
+  c->have_grad = true;
+  return PC_OK;
+}
+
+extern "C" int pc_get_stats(pc_ctx* c, pc_stats* out) {
+  if (!c || !out) return PC_EINVAL;
+  PC_CUDA_TRY(cudaDeviceSynchronize());
+  memset(out, 0, sizeof(*out));
+  int st = 0;
+  PC_CUDA_TRY(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+  out->iterations = c->iterations;
+  out->unconverged_k = c->unconv;
+  out->nk = c->nk;
+  out->N = c->N;
+  out->block = c->m;
+  if (c->have_bands && c->nk > 0) {
+    const int nvec = c->nk * c->m;
+    double* h = (double*)malloc(sizeof(double) * nvec);
+    if (h) {
+      cudaMemcpy(h, c->rnormd, sizeof(double) * nvec, cudaMemcpyDeviceToHost);
+      double mx = 0;
+      for (int k = 0; k < c->nk; ++k)
+        for (int j = 0; j < c->nb; ++j) mx = std::max(mx, h[k * c->m + j]);
+      out->max_residual = mx;
+      free(h);
+    }
+  }
+  if (st == PC_OK && c->unconv > 0) st = PC_ENOCONV;
+  float ms = 0;
+  if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) out->ms_bands = ms;
+  out->status = st;
+  return st;
+}
+
+extern "C" int pc_clear_status(pc_ctx* c) {
+  if (!c) return PC_EINVAL;
+  PC_CUDA_TRY(cudaMemset(c->status, 0, sizeof(int)));
+  return PC_OK;
+}
+
+extern "C" int pc_export(pc_ctx* c, int which, double* host, long long cap, long long* count) {
+  if (!c || !count) return PC_EINVAL;
+  const long long N = c->N, NN = N * N, L = c->L;
+  const void* src = nullptr;
+  long long n = 0;
+  switch (which) {
+    case PC_EXPORT_SFAC: if (!c->have_design) return PC_ESTATE; src = c->sfac; n = 3 * L * L * L * 2; break;
+    case PC_EXPORT_TOEP: if (!c->have_design) return PC_ESTATE; src = c->T; n = 3 * NN * 2; break;
+    case PC_EXPORT_WINV: if (!c->have_design) return PC_ESTATE; src = c->W; n = 2 * NN * 2; break;
+    case PC_EXPORT_LAMBDA: if (!c->have_bands) return PC_ESTATE; n = (long long)c->nk * c->nb; break;
+    case PC_EXPORT_EIGVEC: if (!c->have_bands) return PC_ESTATE; n = (long long)c->nk * c->nb * 3 * N * 2; break;
+    case PC_EXPORT_WEIGHT: if (!c->have_grad) return PC_ESTATE; src = c->weights; n = (long long)c->nk * c->nb; break;
+    default: return PC_EINVAL;
+  }
+  *count = n;
+  if (!host || cap < n) return PC_OK;
+  PC_CUDA_TRY(cudaDeviceSynchronize());
+  if (which == PC_EXPORT_LAMBDA) {
+    PC_CUDA_TRY(cudaMemcpy(host, c->lam_nd, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    for (long long i = 0; i < n; ++i) host[i] *= c->lref;
+    return PC_OK;
+  }
+  if (which == PC_EXPORT_EIGVEC) {
+    const long long per = 3 * N * 2;
+    const double sc = 1.0 / std::sqrt(c->sO);
+    for (int k = 0; k < c->nk; ++k) {
+      PC_CUDA_TRY(cudaMemcpy(host + (long long)k * c->nb * per, c->Th + (long long)k * c->m * 3 * N,
+                             sizeof(double) * per * c->nb, cudaMemcpyDeviceToHost));
+    }
+    for (long long i = 0; i < n; ++i) host[i] *= sc;
+    return PC_OK;
+  }
+  PC_CUDA_TRY(cudaMemcpy(host, src, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  return PC_OK;
+}
+
+extern "C" int pc_apply_operator(pc_ctx* c, int k, int ncols, const double* x, double* ax, double* ox, void* stream) {
+  if (!c || !x || !ax || !ox || ncols < 1) return PC_EINVAL;
+  if (!c->have_design || c->nk == 0) return PC_ESTATE;
+  if (k < 0 || k >= c->nk || ncols > c->nk * c->m) return PC_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double two_pi = 2.0 * M_PI;
+  const double epi = two_pi * two_pi * c->V * c->V;  // SI: (2 pi V)^2
+  return apply_fp64(c, (const double2*)x, (double2*)ax, (double2*)ox, ncols, ncols, c->Q + 3LL * k, epi, 1.0,
+                    c->Ed, c->Sd, s);
+}

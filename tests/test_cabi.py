@@ -1,0 +1,62 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared entry point,
+and rejects bad arguments on the host before touching the device."""
+import os
+import re
+
+import pytest
+
+import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    from paper_1603_06855_gb300 import binding as B, build_lib
+    if not os.path.exists(B.LIB_PATH):
+        build_lib.build()
+    return B
+
+
+def test_header_symbols_exported():
+    B = _lib()
+    header = open(os.path.join(ROOT, "include", "phononic.h")).read()
+    declared = set(re.findall(r"\b(pc_[a-z_]+)\s*\(", header))
+    assert declared == set(B.EXPORTED)
+    lib = B.load()
+    for name in declared:
+        assert hasattr(lib, name)
+
+
+def test_strerror():
+    B = _lib()
+    assert B.pc_strerror(0) == "PC_OK"
+    assert B.pc_strerror(2) == "PC_EALIAS"
+    assert B.pc_strerror(99) == "PC_UNKNOWN"
+
+
+def _params(**kw):
+    B = _lib()
+    base = dict(lattice="sc", n=(8, 8, 8), M=1, nbands=6, phase1=wl.TUNGSTEN_CARBIDE, phase0=wl.EPOXY)
+    base.update(kw)
+    return B.make_params(**base)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(M=0), 1), (dict(M=6), 1), (dict(nbands=0), 1), (dict(nbands=25), 1), (dict(lattice=7), 1),
+    (dict(n=(8, 0, 8)), 1), (dict(penal=0.5), 1), (dict(precision=3), 1), (dict(a=-1.0), 1),
+    (dict(phase1=dict(rho=1.0, E=1.0, nu=0.5)), 1), (dict(phase0=dict(rho=-1.0, E=1.0, nu=0.3)), 1),
+    (dict(n=(8, 4, 8), M=2), 2), (dict(n=(2, 8, 8), M=1), 2),
+])
+def test_create_rejects_bad_parameters(kw, code):
+    B = _lib()
+    assert B.pc_create_rc(_params(**kw)) == code
+
+
+def test_null_handles_rejected():
+    B = _lib()
+    lib = B.load()
+    assert lib.pc_set_kpoints(None, None, 3) == B.PC_EINVAL
+    assert lib.pc_bands(None, None, None) == B.PC_EINVAL
+    assert lib.pc_gap_and_grad(None, 1, 0, None, None, None, None) == B.PC_EINVAL
+    assert lib.pc_clear_status(None) == B.PC_EINVAL
+    lib.pc_destroy(None)

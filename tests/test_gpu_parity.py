@@ -1,0 +1,242 @@
+"""GPU parity: every step of the band + adjoint path against the FP64 oracle, through the C ABI.
+
+Tolerances (stated per result):
+* assembly (structure factors, Toeplitz operators, inverse compliance operators): 1e-12
+  relative to the largest entry (same FP64 sums in a different order);
+* operator apply A(k) x, Omega x: 1e-11 relative (FP64 GEMM vs dense oracle);
+* eigenfrequencies: 1e-9 relative (FP64 form) and 1e-6 (mixed form), measured as
+  |w - w_ref| / max(w_ref, 0.05 max w_ref); Gamma zero modes |lambda| <= 1e-9 lambda_max;
+* gap: same relative bound as the frequencies; gradient: relative L2 1e-5 (FP64) and 1e-4 (mixed).
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import gap as ogap
+from oracle import mixed, sensitivity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_W = {"fp64": 1e-9, "mixed": 1e-6}
+TOL_G = {"fp64": 1e-5, "mixed": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_06855_gb300 import binding, build_lib
+    build_lib.build()
+    binding.load()
+    return binding
+
+
+def solver_for(w, precision, Q=None, **kw):
+    from paper_1603_06855_gb300.solver import BandSolver
+    return BandSolver(w.lattice, w.n, w.M, w.nbands, w.phase1, w.phase0, w.Q if Q is None else Q, w.penal,
+                      precision, w.a, **kw)
+
+
+def omega_err(w_gpu, w_ref, lam_ref=None):
+    """Floored relative frequency error over every band except the Gamma zero modes (those are
+    checked on lambda: |lambda| <= 1e-9 lambda_max on both sides)."""
+    floor = 0.05 * np.max(w_ref)
+    err = np.abs(w_gpu - w_ref) / np.maximum(w_ref, floor)
+    lam_ref = w_ref ** 2 if lam_ref is None else lam_ref
+    zero = np.abs(lam_ref) <= 1e-9 * np.max(np.abs(lam_ref))
+    assert np.all(w_gpu[zero] ** 2 <= 1e-9 * np.max(np.abs(lam_ref))), "zero modes"
+    return np.max(np.where(zero, 0.0, err))
+
+
+def canonical_k(Q):
+    """Index of the first k with the same wavevector (paths revisit vertices)."""
+    out = np.arange(len(Q))
+    for i in range(len(Q)):
+        for j in range(i):
+            if np.array_equal(Q[i], Q[j]):
+                out[i] = out[j]
+                break
+    return out
+
+
+def run_gpu(w, precision, Q=None, **kw):
+    s = solver_for(w, precision, Q, **kw)
+    s.set_design(torch.from_numpy(w.rho.ravel()).cuda())
+    om = s.bands().cpu().numpy()
+    st = s.stats()
+    return s, om, st
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_assembly_matches_element_sums(B, cfg):
+    """Structure factors -> Toeplitz operators (eqs. loop, matrixofintegral, intOmega, intPhi)
+    and the inverse compliance operators, against the oracle's element sums."""
+    w = wl.CONFIGS[cfg]()
+    P = mixed.from_workload(w)
+    s = solver_for(w, "fp64")
+    s.set_design(torch.from_numpy(w.rho.ravel()).cuda())
+    torch.cuda.synchronize()
+    N = P.N
+    T = s.export(B.PC_EXPORT_TOEP).view(np.complex128).reshape(3, N, N)
+    Tr = P.Omega[:N, :N]
+    Tf1 = P.Phi[:N, :N] + 2 * P.Phi[:N, N:2 * N]       # D11 + 2 D12 = f1
+    Tf2 = 0.5 * P.Phi[3 * N:4 * N, 3 * N:4 * N]        # D44 / 2 = f2
+    for got, ref in ((T[0], Tr), (T[1], Tf1), (T[2], Tf2)):
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    W = s.export(B.PC_EXPORT_WINV).view(np.complex128).reshape(2, N, N)
+    for got, ref in ((W[0], np.linalg.inv(Tf1)), (W[1], np.linalg.inv(Tf2))):
+        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+    s.close()
+
+
+@pytest.mark.parametrize("cfg,ks", [(0, [0, 3, 9]), (1, [0, 11]), (2, [5])])
+def test_operator_apply_matches_dense(B, cfg, ks):
+    """A(k) x = H Phi^-1 H^* x and Omega x (eq. matrixform) for seeded random x, several
+    columns that span more than one GEMM tile."""
+    w = wl.CONFIGS[cfg]()
+    P = mixed.from_workload(w)
+    s = solver_for(w, "fp64")
+    s.set_design(torch.from_numpy(w.rho.ravel()).cuda())
+    rng = np.random.default_rng(31 + cfg)
+    n3 = 3 * P.N
+    ncols = 70
+    for k in ks:
+        x = rng.standard_normal((ncols, n3)) + 1j * rng.standard_normal((ncols, n3))
+        ax, ox = s.apply_operator(k, torch.from_numpy(x))
+        A, _ = mixed.operator(P, w.Q[k])
+        ax_ref = (A @ x.T).T
+        ox_ref = (P.Omega @ x.T).T
+        assert np.abs(ax.cpu().numpy() - ax_ref).max() <= 1e-11 * np.abs(ax_ref).max()
+        assert np.abs(ox.cpu().numpy() - ox_ref).max() <= 1e-12 * np.abs(ox_ref).max()
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_bands_match_oracle(B, cfg, precision):
+    w = wl.CONFIGS[cfg]()
+    P = mixed.from_workload(w)
+    lam_ref = mixed.bands(P, w.Q, w.nbands)
+    s, om, st = run_gpu(w, precision)
+    ref = mixed.omega(lam_ref)
+    err = omega_err(om, ref, lam_ref)
+    assert err <= TOL_W[precision], (err, st.iterations, st.max_residual)
+    assert st.status in (B.PC_OK,), B.pc_strerror(st.status)
+    lam = s.export(B.PC_EXPORT_LAMBDA).reshape(w.nk, w.nbands)
+    gam = [k for k in range(w.nk) if np.allclose(w.Q[k], 0)]
+    for k in gam:
+        assert np.all(np.abs(lam[k, :3]) <= 1e-9 * lam_ref.max())
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gap_and_gradient_match_oracle(B, precision):
+    """Config 1: gap(3,4) and gap(6,7) in the omega form and the full 4096-element gradient."""
+    w = wl.config1()
+    P = mixed.from_workload(w)
+    lam_ref, sols = mixed.bands(P, w.Q, w.nbands, keep=True)
+    s, om, st = run_gpu(w, precision)
+    for n_lower in w.gaps:
+        r = ogap.gap(lam_ref, n_lower)
+        g_ref = sensitivity.weighted(P, sols, r.weights)
+        gap, grad = s.gap_and_grad(n_lower)
+        gap = gap.cpu().numpy()[0]
+        grad = grad.cpu().numpy().ravel()
+        assert abs(gap - r.gap) <= TOL_W[precision] * 4 * abs(r.gap) + 1e-12
+        wts = s.export(B.PC_EXPORT_WEIGHT).reshape(w.nk, w.nbands)
+        ck = canonical_k(w.Q)
+        assert np.array_equal(ck[np.nonzero(wts)[0]], ck[np.nonzero(r.weights)[0]])
+        assert np.array_equal(np.nonzero(wts)[1], np.nonzero(r.weights)[1])
+        rel = np.linalg.norm(grad - g_ref) / np.linalg.norm(g_ref)
+        assert rel <= TOL_G[precision], (n_lower, rel)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_weighted_all_bands_gradient(B, precision):
+    """PC_GRAD_ALLBANDS: seeded weights on every (k, band) except the Gamma zero modes."""
+    w = wl.config0()
+    rng = np.random.default_rng(41)
+    rho = np.clip(0.15 + 0.7 * w.rho + 0.05 * rng.standard_normal(w.rho.shape), 0, 1)
+    w.rho = rho
+    P = mixed.from_workload(w)
+    lam_ref, sols = mixed.bands(P, w.Q, w.nbands, keep=True)
+    wts = rng.uniform(-1, 1, size=lam_ref.shape) / lam_ref.max()
+    for k in range(w.nk):
+        if np.allclose(w.Q[k], 0):
+            wts[k, :3] = 0
+    g_ref = sensitivity.weighted(P, sols, wts)
+    s, om, st = run_gpu(w, precision)
+    gap, grad = s.gap_and_grad(mode=B.PC_GRAD_ALLBANDS, weights=torch.from_numpy(wts))
+    assert abs(gap.cpu().numpy()[0] - np.sum(wts * lam_ref)) <= 1e-6 * np.sum(np.abs(wts * lam_ref))
+    rel = np.linalg.norm(grad.cpu().numpy().ravel() - g_ref) / np.linalg.norm(g_ref)
+    assert rel <= TOL_G[precision], rel
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config2_sampled_k(B, precision):
+    """BCC 24^3, N = 343: bands and gap(6,7) gradient on a sample of the 64 k-points."""
+    w = wl.config2()
+    idx = [0, 9, 31, 63]
+    Q = w.Q[idx]
+    P = mixed.from_workload(w)
+    lam_ref, sols = mixed.bands(P, Q, w.nbands, keep=True)
+    s, om, st = run_gpu(w, precision, Q=Q)
+    assert omega_err(om, mixed.omega(lam_ref), lam_ref) <= TOL_W[precision]
+    r = ogap.gap(lam_ref, 6)
+    g_ref = sensitivity.weighted(P, sols, r.weights)
+    gap, grad = s.gap_and_grad(6)
+    rel = np.linalg.norm(grad.cpu().numpy().ravel() - g_ref) / np.linalg.norm(g_ref)
+    assert rel <= TOL_G[precision], rel
+    s.close()
+
+
+def test_edge_cases(B):
+    """Single k, ragged grid (n0 != n1 != n2), the smallest grid n_i = 2M+1, homogeneous
+    designs (closed form), and an out-of-range density flagged as PC_EDOMAIN."""
+    rng = np.random.default_rng(51)
+    # ragged grid, one k
+    rho = rng.uniform(0, 1, (5, 3, 4))
+    w = wl.Workload("ragged", "fcc", (5, 3, 4), 1, 5, np.array([[0.13, 0.27, -0.08]]), rho, 2.0, (2,), 0)
+    P = mixed.from_workload(w)
+    ref = mixed.omega(mixed.bands(P, w.Q, 5))
+    s, om, st = run_gpu(w, "fp64")
+    assert omega_err(om, ref) <= 1e-9
+    s.close()
+    # homogeneous: exact closed form
+    w = wl.homogeneous("bcc", (3, 3, 3), 1, 9, 8, value=1.0)
+    P = mixed.from_workload(w)
+    ref = mixed.omega(mixed.bands(P, w.Q, 9))
+    s, om, st = run_gpu(w, "fp64")
+    assert omega_err(om, ref) <= 1e-9
+    s.close()
+    # out-of-range density
+    w = wl.config0()
+    s = solver_for(w, "fp64")
+    bad = w.rho.ravel().copy()
+    bad[5] = 1.5
+    s.set_design(torch.from_numpy(bad).cuda())
+    st = s.stats()
+    assert st.status == B.PC_EDOMAIN
+    s.close()
+
+
+def test_autograd_function(B):
+    from paper_1603_06855_gb300.solver import BandSolver, gap
+    w = wl.config0()
+    rng = np.random.default_rng(61)
+    rho0 = np.clip(0.1 + 0.8 * w.rho + 0.05 * rng.standard_normal(w.rho.shape), 0, 1)
+    s = BandSolver.from_workload(w)
+    rho = torch.from_numpy(rho0).cuda().requires_grad_(True)
+    g = gap(rho, s, 3)
+    g.backward()
+    P = mixed.build(w.lattice, w.n, w.M, rho0, w.phase1, w.phase0, w.penal)
+    lam, sols = mixed.bands(P, w.Q, w.nbands, keep=True)
+    r = ogap.gap(lam, 3)
+    g_ref = sensitivity.weighted(P, sols, r.weights).reshape(w.n)
+    assert abs(g.item() - r.gap) <= 1e-8
+    assert np.linalg.norm(rho.grad.cpu().numpy() - g_ref) <= 1e-6 * np.linalg.norm(g_ref)
+    s.close()
