@@ -1,0 +1,331 @@
+"""Benchmark: (design . k) band + adjoint solves per second on the FCC primitive cell with
+729 plane waves, 20 bands and 100 k-points per design (32^3 voxels, seeded level-set
+designs, WC / epoxy, SIMP p = 3).
+
+One step = one design evaluation through the C ABI: pc_set_design (SIMP fields,
+structure factors, Toeplitz operators, inverse compliance blocks), pc_bands (batched
+block eigensolver over all 100 k + FP64 Rayleigh-Ritz) and pc_gap_and_grad in the
+all-band weighted form (every (k, band) carries a weight, so the adjoint work is the
+full per-(design . k) work).  The mixed-precision form is the headline; the plain FP64
+GPU form is timed beside it.  --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "design·k band+adjoint solves/s (FCC, N=729, 20 bands) mixed vs FP64; % roofline"
+UNIT = "(design*k)/s"
+WORKLOAD = "fcc32_M4_levelset: FCC primitive cell, 32^3 voxels, N=729 plane waves, 100 k, 20 bands"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--cpu-k", type=int, default=2, help="k-points in the oracle sample")
+    ap.add_argument("--config", type=int, default=3, choices=[1, 2, 3],
+                    help="workload; 3 is the benchmark, 1-2 are smaller cases for profiler captures")
+    return ap.parse_args()
+
+
+def designs(count: int, rank: int, config: int = 3):
+    gen = {1: wl.config1, 2: wl.config2, 3: wl.config3}[config]
+    return [gen(design=rank * 1000 + i) for i in range(count)]
+
+
+def all_band_weights(w):
+    """Dense positive weights on every (k, band) except the Gamma zero modes."""
+    wt = np.full((w.nk, w.nbands), 1.0 / (w.nk * w.nbands))
+    for k in range(w.nk):
+        if np.allclose(w.Q[k], 0.0):
+            wt[k, :3] = 0.0
+    return wt
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(nk_sample: int):
+    """The FP64 oracle (as it stands) on one config-3 design: per-design assembly and
+    Phi^-1 once, then nk_sample wavevectors with their all-band adjoint.  The per
+    (design . k) time is extrapolated to the 100-k design: (t_design + 100 t_k) / 100."""
+    from oracle import mixed, sensitivity
+    w = wl.config3(design=0)
+    t0 = time.perf_counter()
+    P = mixed.from_workload(w)
+    P.phi_inv()
+    t1 = time.perf_counter()
+    wts = all_band_weights(w)
+    ks = np.linspace(1, w.nk - 1, nk_sample).astype(int)
+    grad = np.zeros(w.rho.size)
+    for k in ks:
+        sol = mixed.solve_k(P, w.Q[k], w.nbands, literal=False)
+        for b in range(w.nbands):
+            grad += wts[k, b] * sensitivity.voxel(P, sol.lam[b], sol.theta[:, b], sol.s[:, b])
+    t2 = time.perf_counter()
+    assert np.isfinite(grad).all()
+    t_design, t_k = t1 - t0, (t2 - t1) / len(ks)
+    per = (t_design + w.nk * t_k) / w.nk
+    cores = len(os.sched_getaffinity(0))
+    return {"value": 1.0 / per, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"1 design (assembly + Phi^-1: {t_design:.1f} s) and {len(ks)} of 100 k-points "
+                      f"({t_k:.1f} s each incl. 20-band adjoint); extrapolated to the 100-k design",
+            "seconds": t2 - t0}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    total = args.warmup + args.steps
+    vals = []
+    for i in range(total):
+        r = cpu_baseline(1)
+        if i >= args.warmup:
+            vals.append(r)
+    value = float(np.mean([v["value"] for v in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 100 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"], "sample": vals[0]["sample"], "value": value},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    from paper_1603_06855_gb300 import binding as B
+    from paper_1603_06855_gb300 import build_lib
+    from paper_1603_06855_gb300.solver import BandSolver
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build_lib.build()
+    B.load()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    nsteps = args.warmup + args.steps
+    ws = designs(min(nsteps, 4), rank, args.config)
+    w0 = ws[0]
+    rhos = [torch.from_numpy(w.rho.ravel()).to(dev) for w in ws]
+    wts = torch.from_numpy(all_band_weights(w0)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def run(precision, steps, warmup, profile=False):
+        s = BandSolver.from_workload(w0, precision=precision, device=dev)
+        omega = torch.empty((w0.nk, w0.nbands), dtype=torch.float64, device=dev)
+        gap = torch.empty(1, dtype=torch.float64, device=dev)
+        grad = torch.empty(w0.n, dtype=torch.float64, device=dev)
+        stream = torch.cuda.current_stream(dev)
+
+        def step(i):
+            flush.fill_(float(i))
+            s.set_design(rhos[i % len(rhos)])
+            s.bands(out=omega)
+            s.gap_and_grad(mode=B.PC_GRAD_ALLBANDS, weights=wts, gap_out=gap, grad_out=grad)
+
+        for i in range(warmup):
+            step(i)
+        torch.cuda.synchronize(dev)
+        st0 = s.stats()
+        if st0.status not in (B.PC_OK,):
+            raise RuntimeError(f"warm-up status {B.pc_strerror(st0.status)}")
+        B.pc_clear_status(s.ctx)
+        if profile:
+            B.pc_set_profiling(s.ctx, True)
+        clocks = ClockSampler(local)
+        barrier()
+        torch.cuda.synchronize(dev)
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            step(warmup + i)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ck = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        st = s.stats()
+        return s, ms, st, ck
+
+    # ---- mixed form (headline) ----
+    s_mx, ms_mx, st_mx, ck = run(B.PC_MIXED, args.steps, args.warmup, profile=True)
+    ms_step = ms_mx / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * w0.nk / (ms_step * 1e-3)
+
+    # ---- end to end: host buffers, copies inside the timed region ----
+    rho_h = [torch.from_numpy(w.rho.ravel()).pin_memory() for w in ws]
+    om_h = torch.empty((w0.nk, w0.nbands), dtype=torch.float64).pin_memory()
+    gap_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    grad_h = torch.empty(w0.n, dtype=torch.float64).pin_memory()
+    rho_d = torch.empty(w0.rho.size, dtype=torch.float64, device=dev)
+    om_d = torch.empty((w0.nk, w0.nbands), dtype=torch.float64, device=dev)
+    gap_d = torch.empty(1, dtype=torch.float64, device=dev)
+    grad_d = torch.empty(w0.n, dtype=torch.float64, device=dev)
+
+    def e2e_step(i):
+        rho_d.copy_(rho_h[i % len(rho_h)], non_blocking=True)
+        B.pc_set_design(s_mx.ctx, rho_d.data_ptr(), torch.cuda.current_stream(dev).cuda_stream)
+        s_mx.bands(out=om_d)
+        s_mx.gap_and_grad(mode=B.PC_GRAD_ALLBANDS, weights=wts, gap_out=gap_d, grad_out=grad_d)
+        om_h.copy_(om_d, non_blocking=True)
+        gap_h.copy_(gap_d, non_blocking=True)
+        grad_h.copy_(grad_d, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+
+    e2e_step(0)
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        e2e_step(i)
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+    e2e_value = world * w0.nk / (e2e_ms * 1e-3)
+    h2d = w0.rho.size * 8
+    d2h = (w0.nk * w0.nbands + 1 + w0.rho.size) * 8
+
+    # ---- roofline of the dominant kernel family ----
+    fp64_peak = B.pc_probe(0)
+    fp32_peak = B.pc_probe(1)
+    phases = {
+        "fp64_rayleigh_ritz_gemm": (st_mx.ms_rr_gemm, st_mx.rr_gemm_flops, st_mx.rr_gemm_launches, fp64_peak, "FP64 FMA"),
+        "iteration_operator_apply": (st_mx.ms_iter_apply, st_mx.iter_apply_flops, st_mx.iter_apply_calls, fp32_peak,
+                                     "FP32 FMA"),
+    }
+    dom = max(phases, key=lambda k: phases[k][0])
+    ms_d, fl_d, n_d, peak_gf, peak_kind = phases[dom]
+    achieved = fl_d / (ms_d * 1e-3) / 1e12 if ms_d > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_gf / 1e3, "unit": "TFLOP/s",
+                "frac": achieved / (peak_gf / 1e3) if peak_gf > 0 else None, "traffic": None,
+                "peak_source": f"measured {peak_kind} throughput (pc_probe) on this GPU",
+                "launches_timed": n_d, "share_of_step": ms_d / ms_mx if ms_mx > 0 else None}
+
+    # ---- plain FP64 GPU form ----
+    fp64 = None
+    if not args.no_fp64 and args.fp64_steps > 0:
+        s64, ms64, st64, _ = run(B.PC_FP64, args.fp64_steps, 1, profile=True)
+        v64 = w0.nk / (ms64 / args.fp64_steps * 1e-3)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps, "iterations": st64.iterations,
+                "mixed_over_fp64": value / world / v64}
+        s64.close()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64 (FP32 block iteration, FP64 projected problems and Rayleigh-Ritz)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.config == 3 else ws[0].name, "designs_per_step": 1, "k_per_design": w0.nk, "bands": w0.nbands,
+                       "adjoint": "all-band weighted (every (k, band))",
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "clocks": ck,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(st_mx.launches),
+            "iterations": st_mx.iterations, "max_residual": st_mx.max_residual,
+            "phase_ms_per_step": {"rr_gemm": st_mx.ms_rr_gemm / args.steps,
+                                  "iter_apply": st_mx.ms_iter_apply / args.steps,
+                                  "small_dense": st_mx.ms_small / args.steps,
+                                  "adjoint": st_mx.ms_grad_kernels / args.steps},
+            "fp64_form": fp64,
+            "peaks_measured": {"fp64_tflops": fp64_peak / 1e3, "fp32_tflops": fp32_peak / 1e3}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == 3:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_k)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s_mx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -86,6 +86,16 @@ typedef struct {
   double ms_setup;         /* last pc_set_design, device time */
   double ms_bands;         /* last pc_bands, device time */
   double ms_grad;          /* last pc_gap_and_grad, device time */
+  long long launches;      /* kernel launches since pc_create or the last pc_clear_status */
+  /* Filled while profiling is on (pc_set_profiling), summed since it was switched on: */
+  double ms_rr_gemm;       /* device time of the FP64 operator GEMMs of the Rayleigh-Ritz step */
+  long long rr_gemm_launches;
+  double rr_gemm_flops;    /* their algorithmic flops: 8 N^2 per complex column */
+  double ms_iter_apply;    /* device time of the block iteration's operator applications */
+  long long iter_apply_calls;
+  double iter_apply_flops; /* algorithmic flops: 8 N^2 (6 + 3) per vector */
+  double ms_small;         /* device time of the projected (small dense) problems */
+  double ms_grad_kernels;  /* device time of the adjoint synthesis and reduction */
 } pc_stats;
 
 /* Creates a context: validates the parameters and allocates every per-design
@@ -134,8 +144,18 @@ int pc_gap_and_grad(pc_ctx* ctx, int n_lower, int mode, const double* w_dev,
 /* Synchronises the device and fills *out; returns out->status as well. */
 int pc_get_stats(pc_ctx* ctx, pc_stats* out);
 
-/* Resets the device status word to PC_OK. */
+/* Resets the device status word to PC_OK and the launch counter to zero. */
 int pc_clear_status(pc_ctx* ctx);
+
+/* Switches per-phase device timing on (1) or off (0); switching on zeroes the sums.
+ * Timing records CUDA events on the caller's stream around the timed phases. */
+int pc_set_profiling(pc_ctx* ctx, int on);
+
+/* Measures a device throughput on the current device (synchronous, ~0.1 s):
+ * what = 0: FP64 fused multiply-add rate, what = 1: FP32 fused multiply-add rate,
+ * both in GFLOP/s (2 flops per FMA), with every SM busy.  Not on the hot path.
+ * Errors: PC_EINVAL (bad what or NULL), PC_ECUDA. */
+int pc_probe(int what, double* gflops);
 
 /* Frees every workspace.  NULL is allowed. */
 void pc_destroy(pc_ctx* ctx);

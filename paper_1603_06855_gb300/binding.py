@@ -50,11 +50,21 @@ class pc_stats(ctypes.Structure):
         ("ms_setup", ctypes.c_double),
         ("ms_bands", ctypes.c_double),
         ("ms_grad", ctypes.c_double),
+        ("launches", ctypes.c_longlong),
+        ("ms_rr_gemm", ctypes.c_double),
+        ("rr_gemm_launches", ctypes.c_longlong),
+        ("rr_gemm_flops", ctypes.c_double),
+        ("ms_iter_apply", ctypes.c_double),
+        ("iter_apply_calls", ctypes.c_longlong),
+        ("iter_apply_flops", ctypes.c_double),
+        ("ms_small", ctypes.c_double),
+        ("ms_grad_kernels", ctypes.c_double),
     ]
 
 
 EXPORTED = ["pc_create", "pc_set_kpoints", "pc_set_design", "pc_bands", "pc_gap_and_grad", "pc_get_stats",
-            "pc_clear_status", "pc_destroy", "pc_strerror", "pc_export", "pc_apply_operator"]
+            "pc_clear_status", "pc_set_profiling", "pc_probe", "pc_destroy", "pc_strerror", "pc_export",
+            "pc_apply_operator"]
 
 _lib = None
 
@@ -75,6 +85,8 @@ def load(path: str = LIB_PATH):
     lib.pc_gap_and_grad.argtypes = [P, I, I, P, P, P, P]
     lib.pc_get_stats.argtypes = [P, ctypes.POINTER(pc_stats)]
     lib.pc_clear_status.argtypes = [P]
+    lib.pc_set_profiling.argtypes = [P, I]
+    lib.pc_probe.argtypes = [I, ctypes.POINTER(D)]
     lib.pc_destroy.argtypes = [P]
     lib.pc_destroy.restype = None
     lib.pc_strerror.argtypes = [I]
@@ -163,6 +175,16 @@ def pc_get_stats(ctx: int) -> pc_stats:
 
 def pc_clear_status(ctx: int) -> None:
     _check(load().pc_clear_status(ctx), "pc_clear_status")
+
+
+def pc_set_profiling(ctx: int, on: bool) -> None:
+    _check(load().pc_set_profiling(ctx, 1 if on else 0), "pc_set_profiling")
+
+
+def pc_probe(what: int) -> float:
+    v = ctypes.c_double()
+    _check(load().pc_probe(what, ctypes.byref(v)), "pc_probe")
+    return v.value
 
 
 def pc_destroy(ctx: int) -> None:

@@ -70,6 +70,12 @@ __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(st
     if (e__ != cudaSuccess) return PC_ECUDA;       \
   } while (0)
 
-#define PC_LAUNCH_CHECK() PC_CUDA_TRY(cudaGetLastError())
+// Every kernel launch is followed by this check, which also counts the launch.
+extern long long g_pc_launches;
+#define PC_LAUNCH_CHECK()        \
+  do {                           \
+    ++g_pc_launches;             \
+    PC_CUDA_TRY(cudaGetLastError()); \
+  } while (0)
 
 static inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }

@@ -235,33 +235,31 @@ __device__ void tri_inv_lower(typename cplx_t<R>::type* L, int n, typename cplx_
 
 // Two-sided cyclic Jacobi on Hermitian A (n x n), accumulating V <- V J.  Pairs are
 // scheduled by the circle method so each round rotates n/2 disjoint planes in parallel.
+// A pair is rotated when |a_pq| > eps (sqrt(|a_pp a_qq|) + eps max|a_ii|); the iteration
+// ends after the first sweep that rotates nothing (or max_sweeps).
 template <typename R>
 __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V, int n, int max_sweeps,
                        R* rc, typename cplx_t<R>::type* rs, int* rp, int* rq, R* red, const int* drop) {
   typedef typename cplx_t<R>::type C2;
+  __shared__ int rotated;
   const int npad = n + (n & 1);
   const int npairs = npad / 2;
+  const R eps = SmallEps<R>::v;
+  // scale for the absolute floor
+  R amax = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (!drop[i]) amax = fmax(amax, fabs(A[i * n + i].x));
+  red[threadIdx.x] = amax;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  const R floor_abs = eps * red[0];
+  __syncthreads();
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    // convergence: off-diagonal mass vs total
-    R off = 0, tot = 0;
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-      int i = t / n, c = t % n;
-      if (drop[i] || drop[c]) continue;
-      R v = A[t].x * A[t].x + A[t].y * A[t].y;
-      tot += v;
-      if (i != c) off += v;
-    }
-    red[threadIdx.x] = off;
-    red[blockDim.x + threadIdx.x] = tot;
+    if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if ((int)threadIdx.x < w) { red[threadIdx.x] += red[threadIdx.x + w]; red[blockDim.x + threadIdx.x] += red[blockDim.x + threadIdx.x + w]; }
-      __syncthreads();
-    }
-    R eps = SmallEps<R>::v;
-    bool done = !(red[0] > eps * eps * red[blockDim.x]);
-    __syncthreads();
-    if (done) break;
     for (int round = 0; round < npad - 1; ++round) {
       for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
         int a = (t == 0) ? 0 : ((t - 1 + round) % (npad - 1)) + 1;
@@ -273,12 +271,13 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
           C2 apq = A[p * n + q];
           R beta = sqrt(apq.x * apq.x + apq.y * apq.y);
           R app = A[p * n + p].x, aqq = A[q * n + q].x;
-          if (beta > eps * (fabs(app) + fabs(aqq)) * (R)0.01 && beta > (R)0) {
+          if (beta > eps * (sqrt(fabs(app) * fabs(aqq)) + floor_abs)) {
             R tau = (aqq - app) / (2 * beta);
             R tt = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
             c = (R)1 / sqrt((R)1 + tt * tt);
             R sn = tt * c;
             sp = mk<R>(sn * apq.x / beta, sn * apq.y / beta);
+            rotated = 1;
           }
         }
         rp[t] = p; rq[t] = q; rc[t] = c; rs[t] = sp;
@@ -315,6 +314,9 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
       }
       __syncthreads();
     }
+    bool done = (rotated == 0);
+    __syncthreads();
+    if (done) break;
   }
   __syncthreads();
 }

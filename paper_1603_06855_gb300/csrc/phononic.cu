@@ -21,9 +21,14 @@
 
 extern int g_acc64;     // lobpcg.cu: FP64 accumulation switch (experiments)
 
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
+long long g_pc_launches = 0;
+
+// Per-phase device timing (pc_set_profiling): event pairs recorded on the caller's stream.
+enum { PH_RR_GEMM = 0, PH_ITER_APPLY = 1, PH_SMALL = 2, PH_GRAD = 3, PH_COUNT = 4 };
+struct EventPair {
+  cudaEvent_t a, b;
+  int phase;
+  double flops;
 };
 
 struct pc_ctx {
@@ -64,12 +69,54 @@ struct pc_ctx {
   double2* adj_t2 = nullptr;
   TcPlan* tc = nullptr;
   int debug = 0;  // PC_DEBUG=1 prints the residual history of the block iteration to stderr
+  int profiling = 0;
+  std::vector<EventPair> ev_used, ev_free;
+  double ph_ms[PH_COUNT] = {0, 0, 0, 0};
+  double ph_flops[PH_COUNT] = {0, 0, 0, 0};
+  long long ph_count[PH_COUNT] = {0, 0, 0, 0};
+  long long launch_base = 0;
   unsigned long long seed = 0;  // PC_INIT_SEED: offset of the start-block perturbation
-  int small32 = 0;              // PC_SMALL_FP32=1: projected problems in FP32 (mixed form)
+  int small32 = 1;              // projected problems of the mixed iteration in FP32 (PC_SMALL_FP32=0: FP64)
   int apply64 = 0;              // PC_APPLY64=1: FP64 operator inside the mixed iteration (experiments)
+  int refresh = 40;             // iterations between recomputations of A X, Omega X (PC_REFRESH)
   double2 *sGA = nullptr, *sGO = nullptr, *sC = nullptr, *sCP = nullptr;  // FP64 widened projected problems
   double* slam = nullptr;
 };
+
+// Opens a timed phase on stream s (no-op unless profiling); returns the slot index or -1.
+static int ph_begin(pc_ctx* c, int phase, double flops, cudaStream_t s) {
+  if (!c->profiling) return -1;
+  EventPair e;
+  if (!c->ev_free.empty()) {
+    e = c->ev_free.back();
+    c->ev_free.pop_back();
+  } else {
+    if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) return -1;
+  }
+  e.phase = phase;
+  e.flops = flops;
+  cudaEventRecord(e.a, s);
+  c->ev_used.push_back(e);
+  return (int)c->ev_used.size() - 1;
+}
+static void ph_end(pc_ctx* c, int slot, cudaStream_t s) {
+  if (slot < 0) return;
+  cudaEventRecord(c->ev_used[slot].b, s);
+}
+// Folds finished event pairs into the sums (caller has synchronised).
+static void ph_collect(pc_ctx* c) {
+  for (auto& e : c->ev_used) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+      c->ph_ms[e.phase] += ms;
+      c->ph_flops[e.phase] += e.flops;
+      c->ph_count[e.phase] += 1;
+    }
+    c->ev_free.push_back(e);
+  }
+  c->ev_used.clear();
+  cudaGetLastError();
+}
 
 static const char* kErr[] = {"PC_OK", "PC_EINVAL", "PC_EALIAS", "PC_ENOMEM", "PC_ECUDA",
                              "PC_ESTATE", "PC_ENOCONV", "PC_EDOMAIN", "PC_ETIMEOUT"};
@@ -168,6 +215,8 @@ extern "C" void pc_destroy(pc_ctx* c) {
   dfree(c->Wf); dfree(c->Tf); dfree(c->status);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  for (auto& e : c->ev_used) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  for (auto& e : c->ev_free) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   if (c->h_unconv) cudaFreeHost(c->h_unconv);
   delete c;
 }
@@ -200,16 +249,18 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
     const char* acc = getenv("PC_ACC64");
     
     g_acc64 = (acc && acc[0] == '1') ? 1 : 0;
+    const char* rf = getenv("PC_REFRESH");
+    if (rf && atoi(rf) > 0) c->refresh = atoi(rf);
     const char* a64 = getenv("PC_APPLY64");
     c->apply64 = (a64 && a64[0] == '1') ? 1 : 0;
     const char* s32 = getenv("PC_SMALL_FP32");
-    c->small32 = (s32 && s32[0] == '1') ? 1 : 0;
+    c->small32 = (s32 && s32[0] == '0') ? 0 : 1;
     const char* sd = getenv("PC_INIT_SEED");
     c->seed = sd ? strtoull(sd, nullptr, 10) : 0ull;
 
   }
-  if (c->prm.tol == 0) c->prm.tol = (p->precision == PC_FP64) ? 1e-9 : 1e-4;
-  if (c->prm.max_iter == 0) c->prm.max_iter = (p->precision == PC_FP64) ? 200 : 120;
+  if (c->prm.tol == 0) c->prm.tol = (p->precision == PC_FP64) ? 1e-8 : 1e-4;
+  if (c->prm.max_iter == 0) c->prm.max_iter = (p->precision == PC_FP64) ? 600 : 400;
   c->M2 = M2;
   c->N = N;
   c->L = 4 * p->M + 1;
@@ -336,6 +387,7 @@ extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
 
 extern "C" int pc_set_design(pc_ctx* c, const double* rho, void* stream) {
   if (!c || !rho) return PC_EINVAL;
+  cudaGetLastError();  // launch checks below report only this call's launches
   cudaStream_t s = (cudaStream_t)stream;
   PC_CUDA_TRY(cudaEventRecord(c->ev0, s));
   SetupArgs a;
@@ -385,18 +437,26 @@ template <> struct Ops<float> {
 
 // A x and Omega x for nvec vectors with the per-k geometry Q (vector v belongs to k = v / m).
 static int apply_fp64(pc_ctx* c, const double2* X, double2* AX, double2* OX, int nvec, int m, const double* Q,
-                      double epi, double alpha_omega, double2* E, double2* S, cudaStream_t s) {
+                      double epi, double alpha_omega, double2* E, double2* S, cudaStream_t s, int phase = -1) {
   const int N = c->N;
   const long long NN = (long long)N * N;
+  const double f = 8.0 * (double)N * (double)N;  // algorithmic flops per complex column
   int rc = launch_strain<double>(X, nvec, m, c->geom, Q, E, s);
   if (rc) return rc;
+  int slot = phase >= 0 ? ph_begin(c, phase, f * nvec, s) : -1;
   rc = launch_gemm<double>(N, nvec, N, c->W, N, E, N, S, N, 1.0, s);
+  ph_end(c, slot, s);
   if (rc) return rc;
+  slot = phase >= 0 ? ph_begin(c, phase, f * 5.0 * nvec, s) : -1;
   rc = launch_gemm<double>(N, 5 * nvec, N, c->W + NN, N, E + (long long)nvec * N, N, S + (long long)nvec * N, N, 1.0, s);
+  ph_end(c, slot, s);
   if (rc) return rc;
   rc = launch_epilogue<double>(S, nvec, m, c->geom, Q, epi, epi, AX, s);
   if (rc) return rc;
-  return launch_gemm<double>(N, 3 * nvec, N, c->T, N, X, N, OX, N, alpha_omega, s);
+  slot = phase >= 0 ? ph_begin(c, phase, f * 3.0 * nvec, s) : -1;
+  rc = launch_gemm<double>(N, 3 * nvec, N, c->T, N, X, N, OX, N, alpha_omega, s);
+  ph_end(c, slot, s);
+  return rc;
 }
 
 static int apply_fp32(pc_ctx* c, const float2* X, float2* AX, float2* OX, int nvec, int m, cudaStream_t s) {
@@ -454,12 +514,12 @@ static UpdateArgs<R> upd(pc_ctx* c, int nblk, int identity_last, const void* Cma
   return u;
 }
 
-static const int kRefresh = 10;
 
 // The projected problems (Rayleigh-Ritz pencil, conjugate-direction coefficients and the
-// Cholesky-QR of the search directions) run in FP64 for both precisions: in the mixed form
-// their FP32 Gram inputs are widened, solved in FP64 and the coefficients narrowed again.
-// PC_SMALL_FP32=1 keeps them in FP32 (for experiments).
+// Cholesky-QR of the search directions) of the mixed form's block iteration take FP32
+// Gram matrices; they are solved in FP32 (their inputs carry FP32 accuracy, and an FP64
+// solve costs ~60x more on this part's FP64 units).  PC_SMALL_FP32=0 widens them to FP64
+// (for experiments).  The final Rayleigh-Ritz step always runs in FP64 on FP64 Grams.
 template <typename R> struct SmallTol;
 template <> struct SmallTol<double> { static constexpr double pdir_abs = 1e-26; };
 template <> struct SmallTol<float> { static constexpr double pdir_abs = 1e-12; };
@@ -547,10 +607,12 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
   c->unconv = nk;
   for (it = 0; it < c->prm.max_iter; ++it) {
     // The products A X and Omega X are carried along by the same linear combinations as X;
-    // their rounding drifts away from the true products.  Every kRefresh iterations they
+    // their rounding drifts away from the true products.  Every c->refresh iterations they
     // are recomputed from X and the conjugate block is restarted.
-    if (it > 0 && it % kRefresh == 0) {
+    if (it > 0 && it % c->refresh == 0) {
+      int sl = ph_begin(c, PH_ITER_APPLY, 8.0 * c->N * (double)c->N * 9.0 * nk * m, s);
       TRY(apply_R<R>(c, X, AX, OX, s));
+      ph_end(c, sl, s);
       hasP = false;
     }
     TRY(launch_resnorm<R>(AX, OX, lam, nk, m, nb, n3, c->prm.tol, c->rnorm, c->active, c->kdone, c->d_unconv, s));
@@ -589,12 +651,18 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
       u.out[0] = Wb;
       TRY(launch_update<R>(u, s));
     }
-    TRY(apply_R<R>(c, Wb, AW, OW, s));
+    {
+      int sl = ph_begin(c, PH_ITER_APPLY, 8.0 * c->N * (double)c->N * 9.0 * nk * m, s);
+      TRY(apply_R<R>(c, Wb, AW, OW, s));
+      ph_end(c, sl, s);
+    }
     // W <- W T with T^H (W^H Omega W) T = I, dependent directions dropped
     {
       BlockList<R> A1 = {{Wb, nullptr, nullptr}}, B1 = {{OW, nullptr, nullptr}};
       TRY(launch_gram<R>(A1, 1, B1, 1, nk, m, n3, (R)1, part, GO, s));
+      int sl = ph_begin(c, PH_SMALL, 0.0, s);
       TRY(small_chol_any<R>(c, GO, m, Cc, s));
+      ph_end(c, sl, s);
       UpdateArgs<R> u = upd<R>(c, 1, 0, Cc, (long long)m * m, m, m);
       u.in[0][0] = Wb; u.in[1][0] = AW; u.in[2][0] = OW;
       u.out[0] = Wb; u.out[1] = AW; u.out[2] = OW;
@@ -606,7 +674,11 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
     BlockList<R> S1 = {{X, Wb, P}}, SA = {{AX, AW, AP}}, SO = {{OX, OW, OP}};
     TRY(launch_gram<R>(S1, ns, SA, ns, nk, m, n3, (R)1, part, GA, s));
     TRY(launch_gram<R>(S1, ns, SO, ns, nk, m, n3, (R)1, part, GO, s));
-    TRY(small_rr_any<R>(c, GA, GO, n, m, c->kdone, lam, Cc, Ct, s));
+    {
+      int sl = ph_begin(c, PH_SMALL, 0.0, s);
+      TRY(small_rr_any<R>(c, GA, GO, n, m, c->kdone, lam, Cc, Ct, s));
+      ph_end(c, sl, s);
+    }
     {
       UpdateArgs<R> u = upd<R>(c, ns, 0, Cc, (long long)n * m, m, m);
       u.in[0][0] = X; u.in[0][1] = Wb; u.in[0][2] = P;
@@ -645,7 +717,7 @@ static int fp64_rayleigh_ritz(pc_ctx* c, cudaStream_t s) {
   } else {
     X = (const double2*)c->blk[0];
   }
-  rc = apply_fp64(c, X, c->AXd, c->OXd, (int)nvec, m, c->Q, c->cA, 1.0 / c->sO, c->Ed, c->Sd, s);
+  rc = apply_fp64(c, X, c->AXd, c->OXd, (int)nvec, m, c->Q, c->cA, 1.0 / c->sO, c->Ed, c->Sd, s, PH_RR_GEMM);
   if (rc) return rc;
   BlockList<double> A1 = {{X, nullptr, nullptr}}, B1 = {{c->AXd, nullptr, nullptr}}, B2 = {{c->OXd, nullptr, nullptr}};
   rc = launch_gram<double>(A1, 1, B1, 1, nk, m, n3, 1.0, c->gpartd, c->GAd, s);
@@ -689,6 +761,7 @@ static int fp64_rayleigh_ritz(pc_ctx* c, cudaStream_t s) {
 
 extern "C" int pc_bands(pc_ctx* c, double* omega, void* stream) {
   if (!c || !omega) return PC_EINVAL;
+  cudaGetLastError();  // launch checks below report only this call's launches
   if (!c->have_design || c->nk == 0) return PC_ESTATE;
   cudaStream_t s = (cudaStream_t)stream;
   PC_CUDA_TRY(cudaEventRecord(c->ev0, s));
@@ -711,6 +784,7 @@ extern "C" int pc_gap_and_grad(pc_ctx* c, int n_lower, int mode, const double* w
   if (mode == PC_GRAD_ALLBANDS && !w) return PC_EINVAL;
   if (mode != PC_GRAD_ALLBANDS && (n_lower < 1 || n_lower >= c->nb)) return PC_EINVAL;
   if (!c->have_bands) return PC_ESTATE;
+  cudaGetLastError();  // launch checks below report only this call's launches
   cudaStream_t s = (cudaStream_t)stream;
   PC_CUDA_TRY(cudaEventRecord(c->ev0, s));
   GapArgs g;
@@ -746,7 +820,9 @@ extern "C" int pc_gap_and_grad(pc_ctx* c, int n_lower, int mode, const double* w
     a.dchi = c->dchi;
     a.t2 = c->adj_t2;
     a.grad = grad;
+    int sl = ph_begin(c, PH_GRAD, 0.0, s);
     rc = launch_adjoint(a, s);
+    ph_end(c, sl, s);
     if (rc) return rc;
   }
   PC_CUDA_TRY(cudaEventRecord(c->ev1, s));
@@ -779,7 +855,18 @@ extern "C" int pc_get_stats(pc_ctx* c, pc_stats* out) {
   }
   if (st == PC_OK && c->unconv > 0) st = PC_ENOCONV;
   float ms = 0;
-  if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) out->ms_bands = ms;
+  if (c->have_design && cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) out->ms_bands = ms;
+  cudaGetLastError();  // a query on events of an unfinished call must not leak into later launch checks
+  out->launches = g_pc_launches - c->launch_base;
+  ph_collect(c);
+  out->ms_rr_gemm = c->ph_ms[PH_RR_GEMM];
+  out->rr_gemm_launches = c->ph_count[PH_RR_GEMM];
+  out->rr_gemm_flops = c->ph_flops[PH_RR_GEMM];
+  out->ms_iter_apply = c->ph_ms[PH_ITER_APPLY];
+  out->iter_apply_calls = c->ph_count[PH_ITER_APPLY];
+  out->iter_apply_flops = c->ph_flops[PH_ITER_APPLY];
+  out->ms_small = c->ph_ms[PH_SMALL];
+  out->ms_grad_kernels = c->ph_ms[PH_GRAD];
   out->status = st;
   return st;
 }
@@ -787,6 +874,61 @@ extern "C" int pc_get_stats(pc_ctx* c, pc_stats* out) {
 extern "C" int pc_clear_status(pc_ctx* c) {
   if (!c) return PC_EINVAL;
   PC_CUDA_TRY(cudaMemset(c->status, 0, sizeof(int)));
+  c->launch_base = g_pc_launches;
+  return PC_OK;
+}
+
+extern "C" int pc_set_profiling(pc_ctx* c, int on) {
+  if (!c) return PC_EINVAL;
+  PC_CUDA_TRY(cudaDeviceSynchronize());
+  ph_collect(c);
+  for (int i = 0; i < PH_COUNT; ++i) { c->ph_ms[i] = 0; c->ph_flops[i] = 0; c->ph_count[i] = 0; }
+  c->profiling = on ? 1 : 0;
+  return PC_OK;
+}
+
+// FMA throughput probe: every thread runs 8 independent FMA chains.
+template <typename T>
+__global__ void k_fma_probe(T* out, int iters, T a, T b) {
+  T x[8];
+  for (int i = 0; i < 8; ++i) x[i] = (T)(threadIdx.x + i);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = x[i] * a + b;
+  }
+  T s = 0;
+  for (int i = 0; i < 8; ++i) s += x[i];
+  if (s == (T)-1.2345) out[blockIdx.x] = s;  // keeps the chains alive
+}
+
+extern "C" int pc_probe(int what, double* gflops) {
+  if (!gflops || (what != 0 && what != 1)) return PC_EINVAL;
+  int dev = 0, sms = 0;
+  PC_CUDA_TRY(cudaGetDevice(&dev));
+  PC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  void* out = nullptr;
+  PC_CUDA_TRY(cudaMalloc(&out, 8 * 65536));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = sms * 8, threads = 256;
+  const int iters = (what == 0) ? 2048 : 65536;
+  double best = 0;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0);
+    if (what == 0) k_fma_probe<double><<<blocks, threads>>>((double*)out, iters, 0.999999, 1e-7);
+    else k_fma_probe<float><<<blocks, threads>>>((float*)out, iters, 0.999999f, 1e-7f);
+    cudaEventRecord(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { cudaFree(out); return PC_ECUDA; }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    double fl = 2.0 * 8.0 * (double)iters * blocks * threads;
+    if (rep > 0) best = std::max(best, fl / (ms * 1e-3) / 1e9);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  *gflops = best;
   return PC_OK;
 }
 
@@ -828,6 +970,7 @@ extern "C" int pc_export(pc_ctx* c, int which, double* host, long long cap, long
 
 extern "C" int pc_apply_operator(pc_ctx* c, int k, int ncols, const double* x, double* ax, double* ox, void* stream) {
   if (!c || !x || !ax || !ox || ncols < 1) return PC_EINVAL;
+  cudaGetLastError();  // launch checks below report only this call's launches
   if (!c->have_design || c->nk == 0) return PC_ESTATE;
   if (k < 0 || k >= c->nk || ncols > c->nk * c->m) return PC_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
