@@ -181,8 +181,9 @@ int pc_export(pc_ctx* ctx, int which, double* host, long long capacity, long lon
  * ncols vectors: x_dev, ax_dev, ox_dev hold ncols x 3N complex (interleaved),
  * component-major within a vector (u1 over all waves, then u2, then u3).
  * ax = H Phi^-1 H^* x and ox = Omega x (eq. matrixform), SI units, computed with the
- * FP64 operator path.  Requires pc_set_design and pc_set_kpoints.
- * Errors: PC_EINVAL, PC_ESTATE, PC_ECUDA. */
+ * context's block-iteration operator: FP64 GEMMs for PC_FP64; for PC_MIXED, FP32
+ * vectors and split-BF16 tensor-core products.  ncols <= nk * (bands + guard).
+ * Requires pc_set_design and pc_set_kpoints.  Errors: PC_EINVAL, PC_ESTATE, PC_ECUDA. */
 int pc_apply_operator(pc_ctx* ctx, int k, int ncols, const double* x_dev,
                       double* ax_dev, double* ox_dev, void* stream);
 

@@ -388,3 +388,13 @@ int launch_real_d2f(const double* src, float* dst, long long n, cudaStream_t s) 
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
+
+__global__ void k_scale_d2(double2* __restrict__ x, long long n, double s) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) { x[t].x *= s; x[t].y *= s; }
+}
+int launch_scale_d2(double2* x, long long n, double s, cudaStream_t st) {
+  k_scale_d2<<<cdiv(n, 256), 256, 0, st>>>(x, n, s);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}

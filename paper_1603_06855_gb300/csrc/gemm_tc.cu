@@ -1,7 +1,436 @@
+// Split-BF16 tensor-core application of the condensed operator for the mixed form.
+//
+// Complex N x N operators (the two inverse compliance blocks and the density block) act on
+// complex vectors through their real embedding: row 2p+r, column 2q+r' holds
+// [[Re, -Im], [Im, Re]] of entry (p, q), so a complex column stored as interleaved
+// (re, im) pairs is a real column of length 2N and the product comes out interleaved.
+// Both operands are split into three bf16 slices, x = x_hi + x_mid + x_lo (about 24
+// significant bits, i.e. FP32 precision), and the product is accumulated in FP32 from the
+// six slice products whose order is at most 2^-16: hh, hm, mh, hl, mm, lh.  Sixteen bits
+// per operand are not enough on high-contrast cells: the high-wave-number rows of the
+// stress product come out of strongly cancelling sums and stall the block iteration near
+// a 1e-3 residual.
+//
+// GEMM kernel (sm_103a): C[col][row] = sum_k A[row][k] B[col][k], both operands K-major
+// bf16 in global memory, loaded by TMA (128-byte swizzle) into a 2-stage shared-memory
+// ring; one thread issues tcgen05.mma (kind::f16, M = 128, N = 128, K = 16) into an FP32
+// accumulator in tensor memory; four epilogue warps read it back with tcgen05.ld and store
+// FP32.  Warp 0 produces, warp 1 issues MMAs, warps 2-5 drain.  Every mbarrier wait is
+// bounded: on expiry the kernel records PC_ETIMEOUT in the status word and stops waiting.
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include "gemm_tc.h"
-struct TcPlan { int N, nvec; };
-TcPlan* tc_plan_create(int N, int nvec) { TcPlan* p = new TcPlan; p->N = N; p->nvec = nvec; return p; }
-void tc_plan_destroy(TcPlan* p) { delete p; }
-bool tc_available(const TcPlan*) { return false; }
-int tc_prepare_operators(TcPlan*, const double2*, const double2*, double, double, cudaStream_t) { return PC_OK; }
-int tc_apply(TcPlan*, const float2*, float2*, float2*, int, int, Geom, const double*, cudaStream_t) { return PC_EINVAL; }
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BN = 128;
+constexpr int TC_BK = 64;        // bf16 elements per 128-byte swizzle row
+constexpr int TC_STAGES = 2;
+constexpr int A_TILE = TC_BM * TC_BK * 2;   // 16 KB
+constexpr int B_TILE = TC_BN * TC_BK * 2;   // 32 KB
+constexpr int SLICES = 3;
+constexpr int STAGE_BYTES = SLICES * (A_TILE + B_TILE);
+constexpr int SMEM_BYTES = TC_STAGES * STAGE_BYTES + 1024 /* barriers */ + 1024 /* alignment */;
+constexpr long long WAIT_LIMIT = 1ll << 24;  // try_wait polls before giving up (seconds)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false (and PC_ETIMEOUT recorded) when the limit expires.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicCAS(status, 0, PC_ETIMEOUT);
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)1 << 46;                  // descriptor version
+  d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N = TC_BN.
+__host__ __device__ constexpr uint32_t idesc_bf16() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUtensorMap tA_hi,
+                                                    const __grid_constant__ CUtensorMap tA_mid,
+                                                    const __grid_constant__ CUtensorMap tA_lo,
+                                                    const __grid_constant__ CUtensorMap tB_hi,
+                                                    const __grid_constant__ CUtensorMap tB_mid,
+                                                    const __grid_constant__ CUtensorMap tB_lo, int num_kb, int col_base,
+                                                    int ncols, int m_valid, float* __restrict__ C, long long ldc,
+                                                    int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  const uint32_t bars = base + TC_STAGES * STAGE_BYTES;
+  // barrier layout: full[s] at bars + 8 s, empty[s] at bars + 64 + 8 s, accum at bars + 128, tmem slot at bars + 192
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + TC_STAGES * STAGE_BYTES + 192);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * TC_BM;
+  const int n0 = blockIdx.y * TC_BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(bars + 8 * s, 1);
+      mbar_init(bars + 64 + 8 * s, 1);
+    }
+    mbar_init(bars + 128, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int s = kb % TC_STAGES;
+        const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+        if (!mbar_wait(bars + 64 + 8 * s, ph ^ 1u, status)) break;
+        const uint32_t st = base + s * STAGE_BYTES;
+        mbar_expect_tx(bars + 8 * s, STAGE_BYTES);
+        tma_load_2d(st, &tA_hi, bars + 8 * s, kb * TC_BK, m0);
+        tma_load_2d(st + A_TILE, &tA_mid, bars + 8 * s, kb * TC_BK, m0);
+        tma_load_2d(st + 2 * A_TILE, &tA_lo, bars + 8 * s, kb * TC_BK, m0);
+        tma_load_2d(st + 3 * A_TILE, &tB_hi, bars + 8 * s, kb * TC_BK, col_base + n0);
+        tma_load_2d(st + 3 * A_TILE + B_TILE, &tB_mid, bars + 8 * s, kb * TC_BK, col_base + n0);
+        tma_load_2d(st + 3 * A_TILE + 2 * B_TILE, &tB_lo, bars + 8 * s, kb * TC_BK, col_base + n0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16();
+      bool ok = true;
+      for (int kb = 0; kb < num_kb && ok; ++kb) {
+        const int s = kb % TC_STAGES;
+        const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+        ok = mbar_wait(bars + 8 * s, ph, status);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t st = base + s * STAGE_BYTES;
+        const uint64_t ah = sw128_desc(st), am = sw128_desc(st + A_TILE), al = sw128_desc(st + 2 * A_TILE);
+        const uint64_t bh = sw128_desc(st + 3 * A_TILE), bm = sw128_desc(st + 3 * A_TILE + B_TILE);
+        const uint64_t bl = sw128_desc(st + 3 * A_TILE + 2 * B_TILE);
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+          const uint64_t off = (uint64_t)((kk * 32) >> 4);  // 16 bf16 = 32 bytes along K
+          mma_bf16(tmem, ah + off, bh + off, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          mma_bf16(tmem, ah + off, bm + off, idesc, 1u);
+          mma_bf16(tmem, am + off, bh + off, idesc, 1u);
+          mma_bf16(tmem, ah + off, bl + off, idesc, 1u);
+          mma_bf16(tmem, am + off, bm + off, idesc, 1u);
+          mma_bf16(tmem, al + off, bh + off, idesc, 1u);
+        }
+        mma_commit(bars + 64 + 8 * s);  // stage free once these MMAs have read it
+      }
+      mma_commit(bars + 128);           // accumulator complete
+    }
+  } else {
+    // epilogue warps 2..5: lane quadrant (warp % 4) of the accumulator
+    const int quad = warp & 3;
+    const bool ok = mbar_wait(bars + 128, 0u, status);
+    tc_fence_after();
+    const int row = m0 + quad * 32 + lane;
+#pragma unroll 1
+    for (int c = 0; c < TC_BN / 16; ++c) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 16), v);
+      if (!ok || row >= m_valid) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = n0 + c * 16 + j;
+        if (col < ncols) C[(long long)(col_base + col) * ldc + row] = v[j];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TC_BN) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Operand preparation.
+__device__ __forceinline__ void split3_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& mid, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  float r = x - __bfloat162float(hi);
+  mid = __float2bfloat16_rn(r);
+  lo = __float2bfloat16_rn(r - __bfloat162float(mid));
+}
+
+// Real embedding of a complex N x N operator (SI, times scale) into [Mp][Kp] hi / mid / lo.
+__global__ void k_tc_embed(const double2* __restrict__ W, int N, double scale, int Mp, int Kp,
+                           __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ mid,
+                           __nv_bfloat16* __restrict__ lo) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)Mp * Kp) return;
+  int row = (int)(t / Kp), col = (int)(t % Kp);
+  double v = 0.0;
+  if (row < 2 * N && col < 2 * N) {
+    int p = row >> 1, r = row & 1, q = col >> 1, rp = col & 1;
+    double2 w = W[(long long)p * N + q];
+    double x = (r == rp) ? w.x : (r == 0 ? -w.y : w.y);
+    v = x * scale;
+  }
+  __nv_bfloat16 h = __double2bfloat16(v);
+  double r1 = v - (double)__bfloat162float(h);
+  __nv_bfloat16 mm = __double2bfloat16(r1);
+  double r2 = r1 - (double)__bfloat162float(mm);
+  hi[t] = h;
+  mid[t] = mm;
+  lo[t] = __double2bfloat16(r2);
+}
+
+#define RS2 0.70710678118654752440f
+#define RS3 0.57735026918962576451f
+#define RS6 0.40824829046386301637f
+
+// Strain stacks of X (six per vector) and the three displacement components, written as
+// split bf16 K-major columns: E col = s * nvec + vec, X col = vec * 3 + c; K index 2q + {re, im}.
+// Slice t of E sits at E + t * es, of X at X + t * xs.
+__global__ void k_tc_split_strain(const float2* __restrict__ X, int nvec, int m, Geom g, const double* __restrict__ Q,
+                                  int Kp, __nv_bfloat16* __restrict__ E, long long es, __nv_bfloat16* __restrict__ Xs,
+                                  long long xs) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = g.N;
+  const int Kh = Kp / 2;  // complex slots per column (>= N)
+  if (t >= (long long)nvec * Kh) return;
+  int vec = (int)(t / Kh), q = (int)(t % Kh);
+  float2 u0 = make_float2(0.f, 0.f), u1 = u0, u2 = u0;
+  float k0 = 0.f, k1 = 0.f, k2 = 0.f;
+  if (q < N) {
+    const float2* x = X + (long long)vec * 3 * N;
+    u0 = x[q]; u1 = x[N + q]; u2 = x[2 * N + q];
+    int M2 = 2 * g.M + 1, k = vec / m;
+    double a0 = Q[3 * k] + (double)(q / (M2 * M2) - g.M);
+    double a1 = Q[3 * k + 1] + (double)((q / M2) % M2 - g.M);
+    double a2 = Q[3 * k + 2] + (double)(q % M2 - g.M);
+    k0 = (float)(g.T[0] * a0 + g.T[1] * a1 + g.T[2] * a2);
+    k1 = (float)(g.T[3] * a0 + g.T[4] * a1 + g.T[5] * a2);
+    k2 = (float)(g.T[6] * a0 + g.T[7] * a1 + g.T[8] * a2);
+  }
+  float2 e[6];
+  e[0] = make_float2((k0 * u0.x + k1 * u1.x + k2 * u2.x) * RS3, (k0 * u0.y + k1 * u1.y + k2 * u2.y) * RS3);
+  e[1] = make_float2((k0 * u0.x - k1 * u1.x) * RS2, (k0 * u0.y - k1 * u1.y) * RS2);
+  e[2] = make_float2((k0 * u0.x + k1 * u1.x - 2.f * k2 * u2.x) * RS6, (k0 * u0.y + k1 * u1.y - 2.f * k2 * u2.y) * RS6);
+  e[3] = make_float2((k1 * u2.x + k2 * u1.x) * RS2, (k1 * u2.y + k2 * u1.y) * RS2);
+  e[4] = make_float2((k0 * u2.x + k2 * u0.x) * RS2, (k0 * u2.y + k2 * u0.y) * RS2);
+  e[5] = make_float2((k0 * u1.x + k1 * u0.x) * RS2, (k0 * u1.y + k1 * u0.y) * RS2);
+  for (int s = 0; s < 6; ++s) {
+    long long o = ((long long)s * nvec + vec) * Kp + 2 * q;
+    split3_bf16(e[s].x, E[o], E[o + es], E[o + 2 * es]);
+    split3_bf16(e[s].y, E[o + 1], E[o + 1 + es], E[o + 1 + 2 * es]);
+  }
+  const float2 uu[3] = {u0, u1, u2};
+  for (int c = 0; c < 3; ++c) {
+    long long o = ((long long)vec * 3 + c) * Kp + 2 * q;
+    split3_bf16(uu[c].x, Xs[o], Xs[o + xs], Xs[o + 2 * xs]);
+    split3_bf16(uu[c].y, Xs[o + 1], Xs[o + 1 + xs], Xs[o + 1 + 2 * xs]);
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D K-major bf16 tensor map: rows x Kp, box TC_BK x box_rows, 128-byte swizzle.
+bool make_map(CUtensorMap* m, void* ptr, long long rows, int Kp, int box_rows) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+struct TcPlan {
+  int N, nvec_max, Mp, Kp;
+  __nv_bfloat16* Ahi[3];  // W1, W2, T_rho (embedded, scaled)
+  __nv_bfloat16* Amid[3];
+  __nv_bfloat16* Alo[3];
+  __nv_bfloat16 *E, *X;   // three slices each: slice t at + t * (rows * Kp)
+  float2* S;              // FP32 stress stacks [6][nvec][N]
+  CUtensorMap mA_hi[3], mA_mid[3], mA_lo[3], mE[3], mX[3];
+  int* status;
+  bool ok;
+};
+
+TcPlan* tc_plan_create(int N, int nvec, int* status) {
+  TcPlan* p = new TcPlan();  // value-initialised: every pointer starts null
+  p->N = N;
+  p->nvec_max = nvec;
+  p->Mp = ((2 * N + TC_BM - 1) / TC_BM) * TC_BM;
+  p->Kp = ((2 * N + TC_BK - 1) / TC_BK) * TC_BK;
+  p->status = status;
+  p->ok = false;
+  size_t asz = (size_t)p->Mp * p->Kp;
+  bool good = true;
+  for (int i = 0; i < 3; ++i) {
+    good &= cudaMalloc(&p->Ahi[i], asz * 2) == cudaSuccess;
+    good &= cudaMalloc(&p->Amid[i], asz * 2) == cudaSuccess;
+    good &= cudaMalloc(&p->Alo[i], asz * 2) == cudaSuccess;
+  }
+  size_t esz = (size_t)6 * nvec * p->Kp, xsz = (size_t)3 * nvec * p->Kp;
+  good &= cudaMalloc(&p->E, 3 * esz * 2) == cudaSuccess;
+  good &= cudaMalloc(&p->X, 3 * xsz * 2) == cudaSuccess;
+  good &= cudaMalloc(&p->S, (size_t)6 * nvec * N * sizeof(float2)) == cudaSuccess;
+  if (!good) {
+    cudaGetLastError();
+    tc_plan_destroy(p);
+    return nullptr;
+  }
+  good = true;
+  for (int i = 0; i < 3; ++i) {
+    good &= make_map(&p->mA_hi[i], p->Ahi[i], p->Mp, p->Kp, TC_BM);
+    good &= make_map(&p->mA_mid[i], p->Amid[i], p->Mp, p->Kp, TC_BM);
+    good &= make_map(&p->mA_lo[i], p->Alo[i], p->Mp, p->Kp, TC_BM);
+  }
+  for (int t = 0; t < 3; ++t) {
+    good &= make_map(&p->mE[t], p->E + t * esz, (long long)6 * nvec, p->Kp, TC_BN);
+    good &= make_map(&p->mX[t], p->X + t * xsz, (long long)3 * nvec, p->Kp, TC_BN);
+  }
+  p->ok = good;
+  if (cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
+    cudaGetLastError();
+    p->ok = false;
+  }
+  return p;
+}
+
+void tc_plan_destroy(TcPlan* p) {
+  if (!p) return;
+  for (int i = 0; i < 3; ++i) {
+    if (p->Ahi[i]) cudaFree(p->Ahi[i]);
+    if (p->Amid[i]) cudaFree(p->Amid[i]);
+    if (p->Alo[i]) cudaFree(p->Alo[i]);
+  }
+  if (p->E) cudaFree(p->E);
+  if (p->X) cudaFree(p->X);
+  if (p->S) cudaFree(p->S);
+  delete p;
+}
+
+bool tc_available(const TcPlan* p) { return p && p->ok; }
+
+int tc_prepare_operators(TcPlan* p, const double2* W, const double2* T, double w_scale, double t_scale, cudaStream_t s) {
+  if (!p) return PC_OK;
+  const long long NN = (long long)p->N * p->N, n = (long long)p->Mp * p->Kp;
+  const double2* src[3] = {W, W + NN, T};
+  const double sc[3] = {w_scale, w_scale, t_scale};
+  for (int i = 0; i < 3; ++i) {
+    k_tc_embed<<<cdiv(n, 256), 256, 0, s>>>(src[i], p->N, sc[i], p->Mp, p->Kp, p->Ahi[i], p->Amid[i], p->Alo[i]);
+    PC_LAUNCH_CHECK();
+  }
+  return PC_OK;
+}
+
+static int launch_tc_gemm(TcPlan* p, int which_A, const CUtensorMap* b, int col_base, int ncols, float* C,
+                          cudaStream_t s) {
+  dim3 grid(p->Mp / TC_BM, (ncols + TC_BN - 1) / TC_BN);
+  k_tc_gemm<<<grid, 192, SMEM_BYTES, s>>>(p->mA_hi[which_A], p->mA_mid[which_A], p->mA_lo[which_A], b[0], b[1], b[2],
+                                          p->Kp / TC_BK, col_base, ncols,
+                                          2 * p->N, C, 2LL * p->N, p->status);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+int tc_apply(TcPlan* p, const float2* X, float2* AX, float2* OX, int nvec, int m, Geom g, const double* Q,
+             cudaStream_t s) {
+  if (!tc_available(p) || nvec > p->nvec_max) return PC_EINVAL;
+  const long long n = (long long)nvec * (p->Kp / 2);
+  const long long es = (long long)6 * p->nvec_max * p->Kp, xs = (long long)3 * p->nvec_max * p->Kp;
+  k_tc_split_strain<<<cdiv(n, 256), 256, 0, s>>>(X, nvec, m, g, Q, p->Kp, p->E, es, p->X, xs);
+  PC_LAUNCH_CHECK();
+  // E column s * nvec + v holds stack s of vector v (the maps span the plan's capacity).
+  int rc = launch_tc_gemm(p, 0, p->mE, 0, nvec, (float*)p->S, s);
+  if (rc) return rc;
+  rc = launch_tc_gemm(p, 1, p->mE, nvec, 5 * nvec, (float*)p->S, s);
+  if (rc) return rc;
+  rc = launch_epilogue<float>(p->S, nvec, m, g, Q, 1.0f, 1.0f, AX, s);
+  if (rc) return rc;
+  return launch_tc_gemm(p, 2, p->mX, 0, 3 * nvec, (float*)OX, s);
+}

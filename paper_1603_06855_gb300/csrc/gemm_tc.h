@@ -3,7 +3,8 @@
 #include "kernels.h"
 
 struct TcPlan;
-TcPlan* tc_plan_create(int N, int nvec);
+// status: device word that receives PC_ETIMEOUT if a bounded wait expires.
+TcPlan* tc_plan_create(int N, int nvec, int* status);
 void tc_plan_destroy(TcPlan* p);
 bool tc_available(const TcPlan* p);
 // Converts the FP64 operators (W1, W2 in SI; T_rho in SI) into the scaled split-BF16

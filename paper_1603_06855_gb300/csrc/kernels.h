@@ -152,3 +152,4 @@ int launch_adjoint(const AdjointArgs& a, cudaStream_t s);
 int launch_omega(const double* lam_m, int nk, int nb, int m, double lref, double* omega, double* lam_nd,
                  cudaStream_t s);
 int launch_d2f(const double2* src, float2* dst, long long n, double scale, cudaStream_t s);
+int launch_scale_d2(double2* x, long long n, double s, cudaStream_t st);

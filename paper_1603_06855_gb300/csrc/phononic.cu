@@ -68,6 +68,7 @@ struct pc_ctx {
   int *pairs = nullptr, *npairs = nullptr;
   double2* adj_t2 = nullptr;
   TcPlan* tc = nullptr;
+  bool tc_ready = false;        // tensor-core operands prepared for the current design
   int debug = 0;  // PC_DEBUG=1 prints the residual history of the block iteration to stderr
   int profiling = 0;
   std::vector<EventPair> ev_used, ev_free;
@@ -79,6 +80,7 @@ struct pc_ctx {
   int small32 = 1;              // projected problems of the mixed iteration in FP32 (PC_SMALL_FP32=0: FP64)
   int apply64 = 0;              // PC_APPLY64=1: FP64 operator inside the mixed iteration (experiments)
   int refresh = 40;             // iterations between recomputations of A X, Omega X (PC_REFRESH)
+  int use_tc = 1;               // PC_TC=0: FP32 CUDA-core operator GEMM instead of tensor cores
   double2 *sGA = nullptr, *sGO = nullptr, *sC = nullptr, *sCP = nullptr;  // FP64 widened projected problems
   double* slam = nullptr;
 };
@@ -251,6 +253,8 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
     g_acc64 = (acc && acc[0] == '1') ? 1 : 0;
     const char* rf = getenv("PC_REFRESH");
     if (rf && atoi(rf) > 0) c->refresh = atoi(rf);
+    const char* tcv = getenv("PC_TC");
+    c->use_tc = (tcv && tcv[0] == '0') ? 0 : 1;
     const char* a64 = getenv("PC_APPLY64");
     c->apply64 = (a64 && a64[0] == '1') ? 1 : 0;
     const char* s32 = getenv("PC_SMALL_FP32");
@@ -373,7 +377,8 @@ extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
   rc |= dalloc(&c->slam, nvec);
   rc |= dalloc(&c->adj_t2, (size_t)nk * c->nb * 9 * c->M2 * c->prm.n[1] * c->prm.n[2]);
   if (rc == PC_OK && c->prm.precision == PC_MIXED) {
-    c->tc = tc_plan_create(N, (int)nvec);
+    c->tc = tc_plan_create(N, (int)nvec, c->status);
+    c->tc_ready = false;
     if (!c->tc) rc = PC_ENOMEM;
   }
   if (rc != PC_OK) { free_kset(c); return PC_ENOMEM; }
@@ -409,8 +414,12 @@ extern "C" int pc_set_design(pc_ctx* c, const double* rho, void* stream) {
     if (rc) return rc;
     rc = launch_d2f(c->T, c->Tf, NN, 1.0 / c->sO, s);
     if (rc) return rc;
-    rc = tc_prepare_operators(c->tc, c->W, c->T, c->cA, 1.0 / c->sO, s);
-    if (rc) return rc;
+    c->tc_ready = false;
+    if (c->tc) {
+      rc = tc_prepare_operators(c->tc, c->W, c->T, c->cA, 1.0 / c->sO, s);
+      if (rc) return rc;
+      c->tc_ready = true;
+    }
   }
   PC_CUDA_TRY(cudaEventRecord(c->ev1, s));
   c->have_design = true;
@@ -459,27 +468,37 @@ static int apply_fp64(pc_ctx* c, const double2* X, double2* AX, double2* OX, int
   return rc;
 }
 
-static int apply_fp32(pc_ctx* c, const float2* X, float2* AX, float2* OX, int nvec, int m, cudaStream_t s) {
+// Nondimensional A' X and Omega' X for FP32 vectors (vector v at k = v / m of Q): the split-BF16
+// tensor-core path when available (PC_TC=0 selects the FP32 CUDA-core GEMM instead).
+static int apply_fp32(pc_ctx* c, const float2* X, float2* AX, float2* OX, int nvec, int m, const double* Q,
+                      cudaStream_t s) {
   if (c->apply64) {  // experiment switch: FP64 operator on widened FP32 vectors
     const long long n = (long long)nvec * 3 * c->N;
     int rc = launch_convert_f2d(X, c->Xd, n, s);
-    if (!rc) rc = apply_fp64(c, c->Xd, c->AXd, c->OXd, nvec, m, c->Q, c->cA, 1.0 / c->sO, c->Ed, c->Sd, s);
+    if (!rc) rc = apply_fp64(c, c->Xd, c->AXd, c->OXd, nvec, m, Q, c->cA, 1.0 / c->sO, c->Ed, c->Sd, s);
     if (!rc) rc = launch_d2f(c->AXd, AX, n, 1.0, s);
     if (!rc) rc = launch_d2f(c->OXd, OX, n, 1.0, s);
     return rc;
   }
-  if (c->tc && tc_available(c->tc)) return tc_apply(c->tc, X, AX, OX, nvec, m, c->geom, c->Q, s);
+  if (c->use_tc && c->tc && tc_available(c->tc)) {
+    if (!c->tc_ready) {
+      int rc = tc_prepare_operators(c->tc, c->W, c->T, c->cA, 1.0 / c->sO, s);
+      if (rc) return rc;
+      c->tc_ready = true;
+    }
+    return tc_apply(c->tc, X, AX, OX, nvec, m, c->geom, Q, s);
+  }
   const int N = c->N;
   const long long NN = (long long)N * N;
   float2* E = (float2*)c->E;
   float2* S = (float2*)c->S;
-  int rc = launch_strain<float>(X, nvec, m, c->geom, c->Q, E, s);
+  int rc = launch_strain<float>(X, nvec, m, c->geom, Q, E, s);
   if (rc) return rc;
   rc = launch_gemm<float>(N, nvec, N, c->Wf, N, E, N, S, N, 1.0f, s);
   if (rc) return rc;
   rc = launch_gemm<float>(N, 5 * nvec, N, c->Wf + NN, N, E + (long long)nvec * N, N, S + (long long)nvec * N, N, 1.0f, s);
   if (rc) return rc;
-  rc = launch_epilogue<float>(S, nvec, m, c->geom, c->Q, 1.0f, 1.0f, AX, s);
+  rc = launch_epilogue<float>(S, nvec, m, c->geom, Q, 1.0f, 1.0f, AX, s);
   if (rc) return rc;
   return launch_gemm<float>(N, 3 * nvec, N, c->Tf, N, X, N, OX, N, 1.0f, s);
 }
@@ -492,7 +511,7 @@ int apply_R<double>(pc_ctx* c, const double2* X, double2* AX, double2* OX, cudaS
 }
 template <>
 int apply_R<float>(pc_ctx* c, const float2* X, float2* AX, float2* OX, cudaStream_t s) {
-  return apply_fp32(c, X, AX, OX, c->nk * c->m, c->m, s);
+  return apply_fp32(c, X, AX, OX, c->nk * c->m, c->m, c->Q, s);
 }
 
 template <typename R>
@@ -974,6 +993,20 @@ extern "C" int pc_apply_operator(pc_ctx* c, int k, int ncols, const double* x, d
   if (!c->have_design || c->nk == 0) return PC_ESTATE;
   if (k < 0 || k >= c->nk || ncols > c->nk * c->m) return PC_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (c->prm.precision == PC_MIXED) {
+    // the mixed form's operator: FP32 vectors, split-BF16 tensor-core products, SI on return
+    const long long n = (long long)ncols * 3 * c->N;
+    float2* xf = (float2*)c->blk[3];
+    float2* af = (float2*)c->blk[4];
+    float2* of = (float2*)c->blk[5];
+    int rc = launch_d2f((const double2*)x, xf, n, 1.0, s);
+    if (!rc) rc = apply_fp32(c, xf, af, of, ncols, ncols, c->Q + 3LL * k, s);
+    if (!rc) rc = launch_convert_f2d(af, (double2*)ax, n, s);
+    if (!rc) rc = launch_convert_f2d(of, (double2*)ox, n, s);
+    if (!rc) rc = launch_scale_d2((double2*)ax, n, c->sA, s);
+    if (!rc) rc = launch_scale_d2((double2*)ox, n, c->sO, s);
+    return rc;
+  }
   const double two_pi = 2.0 * M_PI;
   const double epi = two_pi * two_pi * c->V * c->V;  // SI: (2 pi V)^2
   return apply_fp64(c, (const double2*)x, (double2*)ax, (double2*)ox, ncols, ncols, c->Q + 3LL * k, epi, 1.0,

@@ -113,6 +113,32 @@ def test_operator_apply_matches_dense(B, cfg, ks):
     s.close()
 
 
+@pytest.mark.parametrize("cfg,ks", [(0, [0, 4]), (1, [3, 20]), (2, [7])])
+def test_mixed_operator_apply(B, cfg, ks):
+    """The mixed form's operator (FP32 vectors, split-BF16 tensor-core products accumulated in
+    FP32) against the dense FP64 operator: relative Frobenius error <= 2e-5 per block and
+    max-entry error <= 1e-4 of the largest entry."""
+    w = wl.CONFIGS[cfg]()
+    P = mixed.from_workload(w)
+    s = solver_for(w, "mixed")
+    s.set_design(torch.from_numpy(w.rho.ravel()).cuda())
+    rng = np.random.default_rng(71 + cfg)
+    n3 = 3 * P.N
+    ncols = min(300, w.nk * min(w.nbands + 4, 24))
+    for k in ks:
+        x = rng.standard_normal((ncols, n3)) + 1j * rng.standard_normal((ncols, n3))
+        ax, ox = s.apply_operator(k, torch.from_numpy(x))
+        A, _ = mixed.operator(P, w.Q[k])
+        ax_ref = (A @ x.T).T
+        ox_ref = (P.Omega @ x.T).T
+        for got, ref in ((ax.cpu().numpy(), ax_ref), (ox.cpu().numpy(), ox_ref)):
+            assert np.linalg.norm(got - ref) <= 2e-5 * np.linalg.norm(ref)
+            assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+    st = s.stats()
+    assert st.status == B.PC_OK, B.pc_strerror(st.status)
+    s.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("cfg", [0, 1])
 def test_bands_match_oracle(B, cfg, precision):
