@@ -35,6 +35,7 @@ extern "C" {
 #define PC_ENOCONV   6  /* device status: eigensolver hit max_iter for some k (outputs written) */
 #define PC_EDOMAIN   7  /* device status: a density outside [0,1] or not finite */
 #define PC_ETIMEOUT  8  /* device status: a bounded device-side wait expired */
+#define PC_ETOOBIG   9  /* the problem exceeds the fixed working space of an allocation-free call */
 
 /* Lattices (Methods, "Study of cubic unit cells"): primitive cells of the cubic
  * Bravais lattices, vectors along the cube edges (SC), body diagonals (BCC) and
@@ -186,6 +187,29 @@ int pc_export(pc_ctx* ctx, int which, double* host, long long capacity, long lon
  * Requires pc_set_design and pc_set_kpoints.  Errors: PC_EINVAL, PC_ESTATE, PC_ECUDA. */
 int pc_apply_operator(pc_ctx* ctx, int k, int ncols, const double* x_dev,
                       double* ax_dev, double* ox_dev, void* stream);
+
+/* --- Allocation-free entry point (no counterpart in the paper) ---
+ *
+ * For callers that may not allocate device memory once they are running: processes that
+ * reserve their whole device-memory budget at start-up, loops that cannot afford the latency
+ * or the implicit synchronisation of an allocation, and hosts whose allocator is not
+ * available to library code.  Computes, without pc_create and without allocating, the SIMP
+ * fields of a design and the structure factors of density and of the two compliance moduli
+ * (Methods, eq. loop), exactly as pc_set_design does: sfac_dev receives 3 x (4M+1)^3 complex
+ * values (interleaved re, im; density, f1 = (1-2nu)/E, f2 = (1+nu)/E), the same layout as
+ * pc_export(PC_EXPORT_SFAC).  Reads n, M, phase0, phase1 and penal from params (the
+ * structure factors in fractional coordinates do not depend on the lattice).
+ *
+ * Working space: one fixed 5 MiB array in device memory, which every GPU that loads this
+ * library holds until the process exits.  It fits grids up to 40^3 voxels with M <= 5;
+ * larger problems are rejected with PC_ETOOBIG before anything is enqueued.
+ * The first call on a device looks up that array's device address (once per device, with
+ * the device current), so make the first call on each device outside any stream capture.
+ * All calls share the array and every call overwrites it: calls that may overlap on the
+ * GPU (different streams, or threads, on one device) race and must be serialised by the
+ * caller.  Densities outside [0, 1] are clamped.
+ * Errors: PC_EINVAL (NULL or bad parameters), PC_EALIAS, PC_ETOOBIG, PC_ECUDA. */
+int pc_structure_factors_noalloc(const pc_params* params, const double* rho_dev, double* sfac_dev, void* stream);
 
 #ifdef __cplusplus
 }

@@ -10,7 +10,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libphononic.so")
 
-PC_OK, PC_EINVAL, PC_EALIAS, PC_ENOMEM, PC_ECUDA, PC_ESTATE, PC_ENOCONV, PC_EDOMAIN, PC_ETIMEOUT = range(9)
+PC_OK, PC_EINVAL, PC_EALIAS, PC_ENOMEM, PC_ECUDA, PC_ESTATE, PC_ENOCONV, PC_EDOMAIN, PC_ETIMEOUT, PC_ETOOBIG = range(10)
 PC_SC, PC_BCC, PC_FCC = 0, 1, 2
 PC_FP64, PC_MIXED = 0, 1
 PC_GAP_OMEGA, PC_GAP_LAMBDA, PC_GRAD_ALLBANDS = 0, 1, 2
@@ -64,7 +64,7 @@ class pc_stats(ctypes.Structure):
 
 EXPORTED = ["pc_create", "pc_set_kpoints", "pc_set_design", "pc_bands", "pc_gap_and_grad", "pc_get_stats",
             "pc_clear_status", "pc_set_profiling", "pc_probe", "pc_destroy", "pc_strerror", "pc_export",
-            "pc_apply_operator"]
+            "pc_apply_operator", "pc_structure_factors_noalloc"]
 
 _lib = None
 
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
     lib.pc_strerror.restype = ctypes.c_char_p
     lib.pc_export.argtypes = [P, I, P, LL, ctypes.POINTER(LL)]
     lib.pc_apply_operator.argtypes = [P, I, I, P, P, P, P]
+    lib.pc_structure_factors_noalloc.argtypes = [ctypes.POINTER(pc_params), P, P, P]
     for name in EXPORTED:
         if name not in ("pc_destroy", "pc_strerror"):
             getattr(lib, name).restype = I
@@ -202,3 +203,8 @@ def pc_export(ctx: int, which: int):
 
 def pc_apply_operator(ctx: int, k: int, ncols: int, x_ptr: int, ax_ptr: int, ox_ptr: int, stream: int = 0):
     _check(load().pc_apply_operator(ctx, k, ncols, x_ptr, ax_ptr, ox_ptr, stream), "pc_apply_operator")
+
+
+def pc_structure_factors_noalloc(params: pc_params, rho_ptr: int, sfac_ptr: int, stream: int = 0) -> int:
+    """Allocation-free structure factors (return code; 0 on success)."""
+    return load().pc_structure_factors_noalloc(ctypes.byref(params), rho_ptr, sfac_ptr, stream)

@@ -121,10 +121,10 @@ static void ph_collect(pc_ctx* c) {
 }
 
 static const char* kErr[] = {"PC_OK", "PC_EINVAL", "PC_EALIAS", "PC_ENOMEM", "PC_ECUDA",
-                             "PC_ESTATE", "PC_ENOCONV", "PC_EDOMAIN", "PC_ETIMEOUT"};
+                             "PC_ESTATE", "PC_ENOCONV", "PC_EDOMAIN", "PC_ETIMEOUT", "PC_ETOOBIG"};
 
 extern "C" const char* pc_strerror(int code) {
-  if (code < 0 || code > 8) return "PC_UNKNOWN";
+  if (code < 0 || code > 9) return "PC_UNKNOWN";
   return kErr[code];
 }
 
