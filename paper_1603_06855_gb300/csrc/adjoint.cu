@@ -133,97 +133,110 @@ int launch_gap(const GapArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Axis-2 and axis-1 synthesis of field f of pair p:
 //   t2[p][f][g1][j][l] = sum_{g2,g3} c[g1][g2][g3] e^{i pi G2 (2j+1)/n1} e^{i pi G3 (2l+1)/n2}
-// f < 3: displacement component f of theta; f >= 3: stress coordinate f-3.
+// f < 3: displacement component f of theta; f >= 3: stress coordinate f-3.  R is the
+// arithmetic of the synthesis (FP64 for the FP64 form, FP32 for the mixed form).
+template <typename R>
 __global__ void k_adj_synth12(AdjointArgs a) {
+  typedef typename cplx_t<R>::type C2;
   extern __shared__ __align__(16) unsigned char smem[];
   const int p = blockIdx.x, f = blockIdx.y;
   if (p >= *a.npairs) return;
   const int M2 = 2 * a.M + 1, N = a.N, n1 = a.n1, n2 = a.n2;
-  double2* c = (double2*)smem;             // N
-  double2* t1 = c + N;                     // M2*M2*n2
-  double2* ph3 = t1 + M2 * M2 * n2;        // M2*n2
-  double2* ph2 = ph3 + M2 * n2;            // M2*n1
+  C2* c = (C2*)smem;                 // N
+  C2* t1 = c + N;                    // M2*M2*n2
+  C2* ph3 = t1 + M2 * M2 * n2;       // M2*n2
+  C2* ph2 = ph3 + M2 * n2;           // M2*n1
   const int pr = a.pairs[p];
   const int k = pr / a.nb, b = pr % a.nb;
   const long long vec = (long long)k * a.m + b;
   const long long nvec = (long long)a.nk * a.m;
   const double2* src = (f < 3) ? a.theta + (vec * 3 + f) * N : a.sig + ((long long)(f - 3) * nvec + vec) * N;
-  for (int q = threadIdx.x; q < N; q += blockDim.x) c[q] = src[q];
+  for (int q = threadIdx.x; q < N; q += blockDim.x) c[q] = from_d2<R>(src[q]);
   for (int t = threadIdx.x; t < M2 * n2; t += blockDim.x) {
     int g = t / n2, l = t % n2;
-    ph3[t] = phase_pi_over((long long)(g - a.M) * (2 * l + 1), n2);
+    ph3[t] = from_d2<R>(phase_pi_over((long long)(g - a.M) * (2 * l + 1), n2));
   }
   for (int t = threadIdx.x; t < M2 * n1; t += blockDim.x) {
     int g = t / n1, j = t % n1;
-    ph2[t] = phase_pi_over((long long)(g - a.M) * (2 * j + 1), n1);
+    ph2[t] = from_d2<R>(phase_pi_over((long long)(g - a.M) * (2 * j + 1), n1));
   }
   __syncthreads();
   for (int t = threadIdx.x; t < M2 * M2 * n2; t += blockDim.x) {
     int g12 = t / n2, l = t % n2;
-    double2 s = make_double2(0.0, 0.0);
+    C2 s = mk<R>(0, 0);
     for (int g3 = 0; g3 < M2; ++g3) cfma(s, c[g12 * M2 + g3], ph3[g3 * n2 + l]);
     t1[t] = s;
   }
   __syncthreads();
-  double2* out = a.t2 + ((long long)p * 9 + f) * M2 * n1 * n2;
+  C2* out = (C2*)a.t2 + ((long long)p * 9 + f) * M2 * n1 * n2;
   for (long long t = threadIdx.x; t < (long long)M2 * n1 * n2; t += blockDim.x) {
     int l = (int)(t % n2);
     int j = (int)((t / n2) % n1);
     int g1 = (int)(t / ((long long)n1 * n2));
-    double2 s = make_double2(0.0, 0.0);
+    C2 s = mk<R>(0, 0);
     for (int g2 = 0; g2 < M2; ++g2) cfma(s, t1[(g1 * M2 + g2) * n2 + l], ph2[g2 * n1 + j]);
     out[t] = s;
   }
 }
 
-// Axis-0 synthesis fused with the weighted reduction over (k, band).
+// Axis-0 synthesis fused with the weighted reduction over (k, band); the sum over pairs is
+// accumulated in FP64.
+template <typename R>
 __global__ void k_adj_reduce(AdjointArgs a) {
+  typedef typename cplx_t<R>::type C2;
   const int n0 = a.n0, n1 = a.n1, n2 = a.n2, M2 = 2 * a.M + 1;
   const int j = blockIdx.y;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n0 * n2) return;
   const int i = v / n2, l = v % n2;
-  double2 ph[11];
-  for (int g = 0; g < M2; ++g) ph[g] = phase_pi_over((long long)(g - a.M) * (2 * i + 1), n0);
+  C2 ph[11];
+  for (int g = 0; g < M2; ++g) ph[g] = from_d2<R>(phase_pi_over((long long)(g - a.M) * (2 * i + 1), n0));
   const int np = *a.npairs;
   const long long fstride = (long long)M2 * n1 * n2;
   const long long gstride = (long long)n1 * n2;
+  const C2* t2 = (const C2*)a.t2;
   double acc = 0.0;
   for (int p = 0; p < np; ++p) {
     const int pr = a.pairs[p];
     const double w = a.weights[pr];
     const double lam = a.lam[pr] * a.lref;
-    const double2* base = a.t2 + (long long)p * 9 * fstride + (long long)j * n2 + l;
-    double q[9];
+    const C2* base = t2 + (long long)p * 9 * fstride + (long long)j * n2 + l;
+    R q[9];
     for (int f = 0; f < 9; ++f) {
-      double2 s = make_double2(0.0, 0.0);
-      const double2* src = base + f * fstride;
-      for (int g = 0; g < M2; ++g) cfma(s, src[g * gstride], ph[g]);
+      C2 s = mk<R>(0, 0);
+      const C2* srcf = base + f * fstride;
+      for (int g = 0; g < M2; ++g) cfma(s, srcf[g * gstride], ph[g]);
       q[f] = s.x * s.x + s.y * s.y;
     }
-    double u2 = q[0] + q[1] + q[2];
-    double sd = q[4] + q[5] + q[6] + q[7] + q[8];
-    acc += w * (-lam * a.d_rho * u2 - a.two_pi_V_sq * (a.d_f1 * q[3] + a.d_f2 * sd));
+    double u2 = (double)q[0] + q[1] + q[2];
+    double sd = (double)q[4] + q[5] + q[6] + q[7] + q[8];
+    acc += w * (-lam * a.d_rho * u2 - a.two_pi_V_sq * (a.d_f1 * (double)q[3] + a.d_f2 * sd));
   }
   const long long e = ((long long)i * n1 + j) * n2 + l;
   a.grad[e] = acc * a.inv_sO * a.ve * a.dchi[e];
 }
 
-int launch_adjoint(const AdjointArgs& a, cudaStream_t s) {
+template <typename R>
+static int launch_adjoint_t(const AdjointArgs& a, cudaStream_t s) {
+  typedef typename cplx_t<R>::type C2;
   const int M2 = 2 * a.M + 1;
   if (M2 > 11) return PC_EINVAL;
-  size_t sm = sizeof(double2) * ((size_t)a.N + (size_t)M2 * M2 * a.n2 + (size_t)M2 * a.n2 + (size_t)M2 * a.n1);
+  size_t sm = sizeof(C2) * ((size_t)a.N + (size_t)M2 * M2 * a.n2 + (size_t)M2 * a.n2 + (size_t)M2 * a.n1);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_adj_synth12, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_adj_synth12<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
   if (sm > 200 * 1024) return PC_EINVAL;
   dim3 g1(a.max_pairs, 9);
-  k_adj_synth12<<<g1, 256, sm, s>>>(a);
+  k_adj_synth12<R><<<g1, 256, sm, s>>>(a);
   PC_LAUNCH_CHECK();
   dim3 g2(cdiv((long long)a.n0 * a.n2, 256), a.n1);
-  k_adj_reduce<<<g2, 256, 0, s>>>(a);
+  k_adj_reduce<R><<<g2, 256, 0, s>>>(a);
   PC_LAUNCH_CHECK();
   return PC_OK;
+}
+
+int launch_adjoint(const AdjointArgs& a, bool fp32, cudaStream_t s) {
+  return fp32 ? launch_adjoint_t<float>(a, s) : launch_adjoint_t<double>(a, s);
 }

@@ -143,10 +143,11 @@ struct AdjointArgs {
   double two_pi_V_sq;    // (2 pi V)^2
   double ve;             // element volume
   const double* dchi;
-  double2* t2;           // scratch: max_pairs x 9 x M2 x n1 x n2
+  void* t2;              // scratch: max_pairs x 9 x M2 x n1 x n2 complex (FP64 or FP32)
   double* grad;
 };
-int launch_adjoint(const AdjointArgs& a, cudaStream_t s);
+// fp32: synthesis in FP32 (mixed form); the weighted sum is accumulated in FP64 either way.
+int launch_adjoint(const AdjointArgs& a, bool fp32, cudaStream_t s);
 
 // omega[k][b] = sqrt(max(lam_m[k][b] * lref, 0)) and lam_nd[k][b] = lam_m[k][b] for b < nb.
 int launch_omega(const double* lam_m, int nk, int nb, int m, double lref, double* omega, double* lam_nd,

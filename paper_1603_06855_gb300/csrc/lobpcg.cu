@@ -165,90 +165,91 @@ template int launch_update<double>(const UpdateArgs<double>&, cudaStream_t);
 template int launch_update<float>(const UpdateArgs<float>&, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// Small dense Hermitian algebra in shared memory, one CTA (256 threads) per problem.
+// Small dense Hermitian algebra in shared memory, one CTA per problem.  Matrices are stored
+// row-major with an odd leading dimension ld (n + 1 for even n) so that column-wise accesses
+// of consecutive threads fall into distinct banks.
 template <typename R> struct SmallEps;
 template <> struct SmallEps<double> { static constexpr double v = 2.220446049250313e-16; };
 template <> struct SmallEps<float>  { static constexpr float v = 1.1920929e-07f; };
 
-// Unit-diagonal scaling of Hermitian A (and B if given): D_i = 1/sqrt(B_ii) (0 when B_ii <= 0).
-// Cholesky of B with column dropping, in place (lower triangle); drop[j] = 1 for dropped j.
+// Cholesky of Hermitian B (n x n, stride ld) with column dropping, in place (lower
+// triangle); drop[j] = 1 for a pivot at or below tol (dropped rows/columns become e_j).
 template <typename R>
-__device__ void chol_drop(typename cplx_t<R>::type* B, int n, R tol, int* drop) {
+__device__ void chol_drop(typename cplx_t<R>::type* B, int n, int ld, R tol, int* drop) {
   typedef typename cplx_t<R>::type C2;
   for (int j = 0; j < n; ++j) {
     __syncthreads();
-    R d = B[j * n + j].x;
+    R d = B[j * ld + j].x;
     bool dr = !(d > tol);
     __syncthreads();
     if (dr) {
       for (int i = threadIdx.x; i < n; i += blockDim.x)
-        if (i != j) { B[i * n + j] = mk<R>(0, 0); B[j * n + i] = mk<R>(0, 0); }
-      if (threadIdx.x == 0) { B[j * n + j] = mk<R>(1, 0); drop[j] = 1; }
+        if (i != j) { B[i * ld + j] = mk<R>(0, 0); B[j * ld + i] = mk<R>(0, 0); }
+      if (threadIdx.x == 0) { B[j * ld + j] = mk<R>(1, 0); drop[j] = 1; }
       continue;
     }
     R sq = sqrt(d), inv = (R)1 / sq;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) B[i * n + j] = cscale(B[i * n + j], inv);
-    if (threadIdx.x == 0) B[j * n + j] = mk<R>(sq, 0);
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) B[i * ld + j] = cscale(B[i * ld + j], inv);
+    if (threadIdx.x == 0) B[j * ld + j] = mk<R>(sq, 0);
     __syncthreads();
     int nt = n - j - 1;
     for (int t = threadIdx.x; t < nt * nt; t += blockDim.x) {
       int i = j + 1 + t / nt, c = j + 1 + t % nt;
       if (c <= i) {
-        C2 v = B[i * n + c];
-        C2 l1 = B[i * n + j], l2 = B[c * n + j];
+        C2 v = B[i * ld + c];
+        C2 l1 = B[i * ld + j], l2 = B[c * ld + j];
         v.x -= l1.x * l2.x + l1.y * l2.y;
         v.y -= l1.y * l2.x - l1.x * l2.y;
-        B[i * n + c] = v;
+        B[i * ld + c] = v;
       }
     }
   }
   __syncthreads();
 }
 
-// In-place inverse of the lower-triangular L (n x n); upper triangle zeroed.  tmp: n entries.
+// In-place inverse of the lower-triangular L (n x n, stride ld); upper triangle zeroed.
 template <typename R>
-__device__ void tri_inv_lower(typename cplx_t<R>::type* L, int n, typename cplx_t<R>::type* tmp) {
+__device__ void tri_inv_lower(typename cplx_t<R>::type* L, int n, int ld, typename cplx_t<R>::type* tmp) {
   typedef typename cplx_t<R>::type C2;
   for (int j = n - 1; j >= 0; --j) {
     __syncthreads();
-    C2 ljj = L[j * n + j];
+    C2 ljj = L[j * ld + j];
     R den = ljj.x * ljj.x + ljj.y * ljj.y;
     C2 ajj = mk<R>(ljj.x / den, -ljj.y / den);
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) tmp[i] = L[i * n + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) tmp[i] = L[i * ld + j];
     __syncthreads();
     // new L[i][j] = -ajj * sum_{c=j+1..i} Linv[i][c] * old L[c][j]
     for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
       C2 s = mk<R>(0, 0);
-      for (int c = j + 1; c <= i; ++c) cfma(s, L[i * n + c], tmp[c]);
+      for (int c = j + 1; c <= i; ++c) cfma(s, L[i * ld + c], tmp[c]);
       C2 v = cmul(s, ajj);
-      L[i * n + j] = mk<R>(-v.x, -v.y);
+      L[i * ld + j] = mk<R>(-v.x, -v.y);
     }
-    if (threadIdx.x == 0) L[j * n + j] = ajj;
+    if (threadIdx.x == 0) L[j * ld + j] = ajj;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     int i = t / n, c = t % n;
-    if (c > i) L[t] = mk<R>(0, 0);
+    if (c > i) L[i * ld + c] = mk<R>(0, 0);
   }
   __syncthreads();
 }
 
-// Two-sided cyclic Jacobi on Hermitian A (n x n), accumulating V <- V J.  Pairs are
-// scheduled by the circle method so each round rotates n/2 disjoint planes in parallel.
+// Two-sided cyclic Jacobi on Hermitian A (n x n, stride ld), accumulating V <- V J.  Pairs
+// are scheduled by the circle method so each round rotates n/2 disjoint planes in parallel.
 // A pair is rotated when |a_pq| > eps (sqrt(|a_pp a_qq|) + eps max|a_ii|); the iteration
-// ends after the first sweep that rotates nothing (or max_sweeps).
+// ends after the first sweep that rotates nothing (or max_sweeps).  red: 2 blockDim entries.
 template <typename R>
-__device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V, int n, int max_sweeps,
+__device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V, int n, int ld, int max_sweeps,
                        R* rc, typename cplx_t<R>::type* rs, int* rp, int* rq, R* red, const int* drop) {
   typedef typename cplx_t<R>::type C2;
   __shared__ int rotated;
   const int npad = n + (n & 1);
   const int npairs = npad / 2;
   const R eps = SmallEps<R>::v;
-  // scale for the absolute floor
   R amax = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x)
-    if (!drop[i]) amax = fmax(amax, fabs(A[i * n + i].x));
+    if (!drop[i]) amax = fmax(amax, fabs(A[i * ld + i].x));
   red[threadIdx.x] = amax;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -268,9 +269,9 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
         R c = 1;
         C2 sp = mk<R>(0, 0);
         if (q < n && !drop[p] && !drop[q]) {
-          C2 apq = A[p * n + q];
+          C2 apq = A[p * ld + q];
           R beta = sqrt(apq.x * apq.x + apq.y * apq.y);
-          R app = A[p * n + p].x, aqq = A[q * n + q].x;
+          R app = A[p * ld + p].x, aqq = A[q * ld + q].x;
           if (beta > eps * (sqrt(fabs(app) * fabs(aqq)) + floor_abs)) {
             R tau = (aqq - app) / (2 * beta);
             R tt = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
@@ -283,34 +284,36 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
         rp[t] = p; rq[t] = q; rc[t] = c; rs[t] = sp;
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J
+      // columns: A <- A J, V <- V J  (consecutive threads walk rows i of one pair)
       for (int e = threadIdx.x; e < n * npairs; e += blockDim.x) {
-        int t = e % npairs, i = e / npairs;
-        int p = rp[t], q = rq[t];
+        int i = e % n, t = e / n;
+        int q = rq[t];
         if (q >= n) continue;
-        R c = rc[t];
         C2 sp = rs[t];
         if (sp.x == 0 && sp.y == 0) continue;
+        int p = rp[t];
+        R c = rc[t];
         C2 sc = cconj(sp);
-        C2 aip = A[i * n + p], aiq = A[i * n + q];
-        A[i * n + p] = csub(cscale(aip, c), cmul(sc, aiq));
-        A[i * n + q] = cadd(cmul(sp, aip), cscale(aiq, c));
-        C2 vip = V[i * n + p], viq = V[i * n + q];
-        V[i * n + p] = csub(cscale(vip, c), cmul(sc, viq));
-        V[i * n + q] = cadd(cmul(sp, vip), cscale(viq, c));
+        C2 aip = A[i * ld + p], aiq = A[i * ld + q];
+        A[i * ld + p] = csub(cscale(aip, c), cmul(sc, aiq));
+        A[i * ld + q] = cadd(cmul(sp, aip), cscale(aiq, c));
+        C2 vip = V[i * ld + p], viq = V[i * ld + q];
+        V[i * ld + p] = csub(cscale(vip, c), cmul(sc, viq));
+        V[i * ld + q] = cadd(cmul(sp, vip), cscale(viq, c));
       }
       __syncthreads();
-      // rows: A <- J^H A
+      // rows: A <- J^H A  (consecutive threads walk columns j of one pair)
       for (int e = threadIdx.x; e < n * npairs; e += blockDim.x) {
-        int t = e % npairs, j = e / npairs;
-        int p = rp[t], q = rq[t];
+        int j = e % n, t = e / n;
+        int q = rq[t];
         if (q >= n) continue;
-        R c = rc[t];
         C2 sp = rs[t];
         if (sp.x == 0 && sp.y == 0) continue;
-        C2 apj = A[p * n + j], aqj = A[q * n + j];
-        A[p * n + j] = csub(cscale(apj, c), cmul(sp, aqj));
-        A[q * n + j] = cadd(cmul(cconj(sp), apj), cscale(aqj, c));
+        int p = rp[t];
+        R c = rc[t];
+        C2 apj = A[p * ld + j], aqj = A[q * ld + j];
+        A[p * ld + j] = csub(cscale(apj, c), cmul(sp, aqj));
+        A[q * ld + j] = cadd(cmul(cconj(sp), apj), cscale(aqj, c));
       }
       __syncthreads();
     }
@@ -321,29 +324,35 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
   __syncthreads();
 }
 
+#define SMALL_THREADS 512
 template <typename R> struct SmallSmem {
+  static int ld(int n) { return n + ((n & 1) ? 0 : 1); }
   static size_t bytes(int n) {
     typedef typename cplx_t<R>::type C2;
-    return sizeof(C2) * (2 * (size_t)n * n + n + 64) + sizeof(R) * (3 * n + 64 + 512) + sizeof(int) * (3 * n + 128);
+    const int L = ld(n);
+    return sizeof(C2) * (2 * (size_t)n * L + n + 64) + sizeof(R) * (3 * n + 64 + 2 * SMALL_THREADS) +
+           sizeof(int) * (3 * n + 128);
   }
 };
 
 template <typename R>
-__global__ __launch_bounds__(256) void k_small_rr(const typename cplx_t<R>::type* __restrict__ GA,
-                                                  const typename cplx_t<R>::type* __restrict__ GO, int n, int m,
-                                                  R drop_tol, const int* __restrict__ kdone, R* __restrict__ lam_out,
-                                                  typename cplx_t<R>::type* __restrict__ coef, int* status) {
+__global__ __launch_bounds__(SMALL_THREADS) void k_small_rr(const typename cplx_t<R>::type* __restrict__ GA,
+                                                            const typename cplx_t<R>::type* __restrict__ GO, int n, int m,
+                                                            R drop_tol, const int* __restrict__ kdone,
+                                                            R* __restrict__ lam_out,
+                                                            typename cplx_t<R>::type* __restrict__ coef, int* status) {
   typedef typename cplx_t<R>::type C2;
   extern __shared__ __align__(16) unsigned char smem[];
-  C2* A = (C2*)smem;                 // n*n
-  C2* B = A + n * n;                 // n*n
-  C2* tmp = B + n * n;               // n
+  const int ld = n + ((n & 1) ? 0 : 1);
+  C2* A = (C2*)smem;                 // n*ld
+  C2* B = A + n * ld;                // n*ld
+  C2* tmp = B + n * ld;              // n
   C2* rs = tmp + n;                  // 64
   R* D = (R*)(rs + 64);              // n
   R* ev = D + n;                     // n
   R* rc = ev + n;                    // 64
-  R* red = rc + 64;                  // 512
-  R* spare = red + 512;              // n
+  R* red = rc + 64;                  // 2 * SMALL_THREADS
+  R* spare = red + 2 * SMALL_THREADS;  // n
   int* drop = (int*)(spare + n);     // n
   int* perm = drop + n;              // n
   int* rp = perm + n;                // 64
@@ -367,75 +376,69 @@ __global__ __launch_bounds__(256) void k_small_rr(const typename cplx_t<R>::type
     drop[i] = 0;
   }
   __syncthreads();
-  // Hermitian-symmetrised, scaled copies
+  // Hermitian-symmetrised, unit-diagonal-scaled copies
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     int i = t / n, c = t % n;
     C2 a1 = ga[i * n + c], a2 = ga[c * n + i];
     C2 b1 = go[i * n + c], b2 = go[c * n + i];
     R s = D[i] * D[c] * (R)0.5;
-    A[t] = mk<R>((a1.x + a2.x) * s, (a1.y - a2.y) * s);
-    B[t] = mk<R>((b1.x + b2.x) * s, (b1.y - b2.y) * s);
+    A[i * ld + c] = mk<R>((a1.x + a2.x) * s, (a1.y - a2.y) * s);
+    B[i * ld + c] = mk<R>((b1.x + b2.x) * s, (b1.y - b2.y) * s);
   }
   __syncthreads();
-  chol_drop<R>(B, n, drop_tol, drop);
-  tri_inv_lower<R>(B, n, tmp);  // B = Li (lower)
-  // A <- A Li^H, row by row (one warp per row, row staged in tmp-per-warp region of V? use red as scratch)
-  {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int i = warp; i < n; i += nw) {
-      // each lane computes entries j = lane, lane+32, ... of the new row i; old row read from A
-      C2 outv[3];
-      int cnt_j = 0;
-      for (int j = lane; j < n && cnt_j < 3; j += 32, ++cnt_j) {
-        C2 s = mk<R>(0, 0);
-        for (int c = 0; c <= j; ++c) cfmac(s, B[j * n + c], A[i * n + c]);  // sum_c A[i][c] conj(Li[j][c])
-        outv[cnt_j] = s;
-      }
-      __syncwarp();
-      cnt_j = 0;
-      for (int j = lane; j < n && cnt_j < 3; j += 32, ++cnt_j) A[i * n + j] = outv[cnt_j];
-      __syncwarp();
+  chol_drop<R>(B, n, ld, drop_tol, drop);
+  tri_inv_lower<R>(B, n, ld, tmp);  // B = Li (lower)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // A <- A Li^H, one warp per row
+  for (int i = warp; i < n; i += nw) {
+    C2 outv[3];
+    int cj = 0;
+    for (int j = lane; j < n && cj < 3; j += 32, ++cj) {
+      C2 s = mk<R>(0, 0);
+      for (int c = 0; c <= j; ++c) cfmac(s, B[j * ld + c], A[i * ld + c]);  // sum_c A[i][c] conj(Li[j][c])
+      outv[cj] = s;
     }
+    __syncwarp();
+    cj = 0;
+    for (int j = lane; j < n && cj < 3; j += 32, ++cj) A[i * ld + j] = outv[cj];
+    __syncwarp();
   }
   __syncthreads();
-  // A <- Li A, column by column
-  {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int j = warp; j < n; j += nw) {
-      C2 outv[3];
-      int ci = 0;
-      for (int i = lane; i < n && ci < 3; i += 32, ++ci) {
-        C2 s = mk<R>(0, 0);
-        for (int c = 0; c <= i; ++c) cfma(s, B[i * n + c], A[c * n + j]);
-        outv[ci] = s;
-      }
-      __syncwarp();
-      ci = 0;
-      for (int i = lane; i < n && ci < 3; i += 32, ++ci) A[i * n + j] = outv[ci];
-      __syncwarp();
+  // A <- Li A, one warp per column
+  for (int j = warp; j < n; j += nw) {
+    C2 outv[3];
+    int ci = 0;
+    for (int i = lane; i < n && ci < 3; i += 32, ++ci) {
+      C2 s = mk<R>(0, 0);
+      for (int c = 0; c <= i; ++c) cfma(s, B[i * ld + c], A[c * ld + j]);
+      outv[ci] = s;
     }
+    __syncwarp();
+    ci = 0;
+    for (int i = lane; i < n && ci < 3; i += 32, ++ci) A[i * ld + j] = outv[ci];
+    __syncwarp();
   }
   __syncthreads();
   // dropped coordinates: decoupled; Jacobi leaves them alone and the sort puts them last
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     int i = t / n, c = t % n;
-    if (drop[i] || drop[c]) A[t] = mk<R>(0, 0);
+    if (drop[i] || drop[c]) A[i * ld + c] = mk<R>(0, 0);
   }
   __syncthreads();
   // B <- Li^H (conjugate transpose in place): V starts as Li^H so that V J = Li^H Y
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     int i = t / n, c = t % n;
     if (c > i) {
-      C2 lo = B[c * n + i];
-      B[i * n + c] = cconj(lo);
-      B[c * n + i] = mk<R>(0, 0);
+      C2 lo = B[c * ld + i];
+      B[i * ld + c] = cconj(lo);
+      B[c * ld + i] = mk<R>(0, 0);
     } else if (c == i) {
-      B[t] = cconj(B[t]);
+      B[i * ld + c] = cconj(B[i * ld + c]);
     }
   }
   __syncthreads();
-  jacobi<R>(A, B, n, 30, rc, rs, rp, rq, red, drop);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) ev[i] = A[i * n + i].x;
+  jacobi<R>(A, B, n, ld, 30, rc, rs, rp, rq, red, drop);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ev[i] = A[i * ld + i].x;
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     int r = 0;
@@ -467,7 +470,7 @@ __global__ __launch_bounds__(256) void k_small_rr(const typename cplx_t<R>::type
   }
   for (int t = threadIdx.x; t < n * m; t += blockDim.x) {
     int i = t / m, j = t % m;
-    ck[t] = cscale(B[i * n + perm[j]], D[i]);
+    ck[t] = cscale(B[i * ld + perm[j]], D[i]);
   }
   for (int j = threadIdx.x; j < m; j += blockDim.x) lam_out[(long long)k * m + j] = ev[perm[j]];
 }
@@ -483,7 +486,7 @@ int launch_small_rr(const typename cplx_t<R>::type* GA, const typename cplx_t<R>
     attr_set = true;
   }
   if (sm > 200 * 1024) return PC_EINVAL;
-  k_small_rr<R><<<nk, 256, sm, s>>>(GA, GO, n, m, drop_tol, kdone, lam_out, coef, status);
+  k_small_rr<R><<<nk, SMALL_THREADS, sm, s>>>(GA, GO, n, m, drop_tol, kdone, lam_out, coef, status);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
@@ -496,10 +499,11 @@ __global__ __launch_bounds__(256) void k_small_chol(const typename cplx_t<R>::ty
                                                     const typename cplx_t<R>::type* __restrict__ Gref, int rows_ref,
                                                     R rel_tol, typename cplx_t<R>::type* __restrict__ T) {
   typedef typename cplx_t<R>::type C2;
-  __shared__ C2 B[24 * 24];
+  __shared__ C2 B[24 * 25];
   __shared__ C2 tmp[24];
   __shared__ R D[24];
   __shared__ int drop[24];
+  const int ld = m + ((m & 1) ? 0 : 1);
   const int k = blockIdx.x;
   const C2* g = G + (long long)k * m * m;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -517,16 +521,16 @@ __global__ __launch_bounds__(256) void k_small_chol(const typename cplx_t<R>::ty
     int i = t / m, c = t % m;
     C2 b1 = g[i * m + c], b2 = g[c * m + i];
     R s = D[i] * D[c] * (R)0.5;
-    B[t] = mk<R>((b1.x + b2.x) * s, (b1.y - b2.y) * s);
+    B[i * ld + c] = mk<R>((b1.x + b2.x) * s, (b1.y - b2.y) * s);
   }
   __syncthreads();
-  chol_drop<R>(B, m, drop_tol, drop);
-  tri_inv_lower<R>(B, m, tmp);
+  chol_drop<R>(B, m, ld, drop_tol, drop);
+  tri_inv_lower<R>(B, m, ld, tmp);
   C2* tk = T + (long long)k * m * m;
   for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
     int i = t / m, c = t % m;
     // T[i][c] = D_i conj(Li[c][i]); dropped columns vanish
-    C2 v = (c >= i && !drop[c]) ? cscale(cconj(B[c * m + i]), D[i]) : mk<R>(0, 0);
+    C2 v = (c >= i && !drop[c]) ? cscale(cconj(B[c * ld + i]), D[i]) : mk<R>(0, 0);
     tk[t] = v;
   }
 }
@@ -626,8 +630,8 @@ __global__ __launch_bounds__(256) void k_small_pdir(const typename cplx_t<R>::ty
     Mm[t] = mk<R>((s1.x + s2.x) * sc, (s1.y - s2.y) * sc);
   }
   __syncthreads();
-  chol_drop<R>(Mm, m, (R)1e-10, drop);
-  tri_inv_lower<R>(Mm, m, tmp);
+  chol_drop<R>(Mm, m, m, (R)1e-10, drop);
+  tri_inv_lower<R>(Mm, m, m, tmp);
   // cP = Z T with T[i][c] = D_i conj(Li[c][i]) for c >= i and c kept
   for (int t = threadIdx.x; t < n * m; t += blockDim.x) {
     int r = t / m, c = t % m;

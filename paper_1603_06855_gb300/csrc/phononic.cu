@@ -840,7 +840,7 @@ extern "C" int pc_gap_and_grad(pc_ctx* c, int n_lower, int mode, const double* w
     a.t2 = c->adj_t2;
     a.grad = grad;
     int sl = ph_begin(c, PH_GRAD, 0.0, s);
-    rc = launch_adjoint(a, s);
+    rc = launch_adjoint(a, c->prm.precision == PC_MIXED, s);
     ph_end(c, sl, s);
     if (rc) return rc;
   }

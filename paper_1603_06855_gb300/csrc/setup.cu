@@ -134,15 +134,20 @@ __global__ void k_gj_snapshot(const double2* __restrict__ A, int N, long long ms
 __global__ void k_gj_step(double2* __restrict__ A, int N, long long mstride, int k,
                           const double2* __restrict__ row_in, const double2* __restrict__ col_in,
                           double2* __restrict__ row_out, double2* __restrict__ col_out) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int i = blockIdx.y;
-  int z = blockIdx.z;
-  if (j >= N) return;
+  __shared__ double2 ip_s;
+  const int z = blockIdx.z;
   const double2* rk = row_in + (long long)z * N;
   const double2* ck = col_in + (long long)z * N;
-  double2 piv = rk[k];
-  double den = piv.x * piv.x + piv.y * piv.y;
-  double2 ip = make_double2(piv.x / den, -piv.y / den);  // 1 / pivot
+  if (threadIdx.x == 0) {  // 1 / pivot, once per block (FP64 division is expensive here)
+    double2 piv = rk[k];
+    double den = piv.x * piv.x + piv.y * piv.y;
+    ip_s = make_double2(piv.x / den, -piv.y / den);
+  }
+  __syncthreads();
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y;
+  if (j >= N) return;
+  const double2 ip = ip_s;
   double2* a = A + z * mstride + (long long)i * N + j;
   double2 v;
   if (i == k && j == k) v = ip;
