@@ -181,15 +181,16 @@ __global__ void k_adj_synth12(AdjointArgs a) {
 
 // Axis-0 synthesis fused with the weighted reduction over (k, band); the sum over pairs is
 // accumulated in FP64.
-template <typename R>
+template <typename R, int M2>
 __global__ void k_adj_reduce(AdjointArgs a) {
   typedef typename cplx_t<R>::type C2;
-  const int n0 = a.n0, n1 = a.n1, n2 = a.n2, M2 = 2 * a.M + 1;
+  const int n0 = a.n0, n1 = a.n1, n2 = a.n2;
   const int j = blockIdx.y;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n0 * n2) return;
   const int i = v / n2, l = v % n2;
-  C2 ph[11];
+  C2 ph[M2];  // compile-time size and fully unrolled loops keep these in registers
+#pragma unroll
   for (int g = 0; g < M2; ++g) ph[g] = from_d2<R>(phase_pi_over((long long)(g - a.M) * (2 * i + 1), n0));
   const int np = *a.npairs;
   const long long fstride = (long long)M2 * n1 * n2;
@@ -202,9 +203,11 @@ __global__ void k_adj_reduce(AdjointArgs a) {
     const double lam = a.lam[pr] * a.lref;
     const C2* base = t2 + (long long)p * 9 * fstride + (long long)j * n2 + l;
     R q[9];
+#pragma unroll
     for (int f = 0; f < 9; ++f) {
       C2 s = mk<R>(0, 0);
       const C2* srcf = base + f * fstride;
+#pragma unroll
       for (int g = 0; g < M2; ++g) cfma(s, srcf[g * gstride], ph[g]);
       q[f] = s.x * s.x + s.y * s.y;
     }
@@ -232,7 +235,13 @@ static int launch_adjoint_t(const AdjointArgs& a, cudaStream_t s) {
   k_adj_synth12<R><<<g1, 256, sm, s>>>(a);
   PC_LAUNCH_CHECK();
   dim3 g2(cdiv((long long)a.n0 * a.n2, 256), a.n1);
-  k_adj_reduce<R><<<g2, 256, 0, s>>>(a);
+  switch (M2) {
+    case 3: k_adj_reduce<R, 3><<<g2, 256, 0, s>>>(a); break;
+    case 5: k_adj_reduce<R, 5><<<g2, 256, 0, s>>>(a); break;
+    case 7: k_adj_reduce<R, 7><<<g2, 256, 0, s>>>(a); break;
+    case 9: k_adj_reduce<R, 9><<<g2, 256, 0, s>>>(a); break;
+    default: k_adj_reduce<R, 11><<<g2, 256, 0, s>>>(a); break;
+  }
   PC_LAUNCH_CHECK();
   return PC_OK;
 }

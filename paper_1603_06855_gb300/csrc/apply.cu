@@ -188,15 +188,15 @@ __global__ void k_resnorm(const typename cplx_t<R>::type* __restrict__ AX, const
   R l = lam[vec];
   const C2* ax = AX + (long long)vec * n3;
   const C2* ox = OX + (long long)vec * n3;
-  double sa = 0.0, sb = 0.0;
+  R sa = 0, sb = 0;  // per-thread partial sums in the block's own precision
   for (int r = threadIdx.x; r < n3; r += blockDim.x) {
     C2 a = ax[r], o = ox[r];
-    double dx = (double)a.x - (double)l * (double)o.x, dy = (double)a.y - (double)l * (double)o.y;
+    R dx = a.x - l * o.x, dy = a.y - l * o.y;
     sa += dx * dx + dy * dy;
-    sb += (double)o.x * o.x + (double)o.y * o.y;
+    sb += o.x * o.x + o.y * o.y;
   }
-  ra[threadIdx.x] = sa;
-  rb[threadIdx.x] = sb;
+  ra[threadIdx.x] = (double)sa;
+  rb[threadIdx.x] = (double)sb;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) { ra[threadIdx.x] += ra[threadIdx.x + w]; rb[threadIdx.x] += rb[threadIdx.x + w]; }
@@ -262,32 +262,34 @@ __global__ void k_precond(const typename cplx_t<R>::type* __restrict__ AX, const
     w[0] = mk<R>(0, 0); w[N] = mk<R>(0, 0); w[2 * N] = mk<R>(0, 0);
     return;
   }
-  double cm = *chi_mean;
-  double lam_r = pr.lam0 + cm * (pr.lam1 - pr.lam0);
-  double mu_r = pr.mu0 + cm * (pr.mu1 - pr.mu0);
-  double rho_r = pr.rho0 + cm * (pr.rho1 - pr.rho0);
-  double sig = 0.0;
-  for (int j = 0; j < nb; ++j) sig = fmax(sig, (double)lam[k * m + j]);
-  sig = fmax(sig, 1e-6);
-  double K[3];
-  kvec(g, Q, k, q, K);
-  double k2 = K[0] * K[0] + K[1] * K[1] + K[2] * K[2];
-  double a = pr.two_pi_sq_V_over_sA * mu_r * k2 + pr.half_lref_V_over_sA * rho_r * sig;
-  double b = pr.two_pi_sq_V_over_sA * (lam_r + mu_r);
-  double f = b / (a + b * k2);
-  double l = (double)lam[vec];
+  const double cm = *chi_mean;
+  const R lam_r = (R)(pr.lam0 + cm * (pr.lam1 - pr.lam0));
+  const R mu_r = (R)(pr.mu0 + cm * (pr.mu1 - pr.mu0));
+  const R rho_r = (R)(pr.rho0 + cm * (pr.rho1 - pr.rho0));
+  R sig = 0;
+  for (int j = 0; j < nb; ++j) sig = fmax(sig, lam[k * m + j]);
+  sig = fmax(sig, (R)1e-6);
+  double Kd[3];
+  kvec(g, Q, k, q, Kd);
+  const R K0 = (R)Kd[0], K1 = (R)Kd[1], K2 = (R)Kd[2];
+  const R k2 = K0 * K0 + K1 * K1 + K2 * K2;
+  const R a = (R)pr.two_pi_sq_V_over_sA * mu_r * k2 + (R)pr.half_lref_V_over_sA * rho_r * sig;
+  const R b = (R)pr.two_pi_sq_V_over_sA * (lam_r + mu_r);
+  const R ia = (R)1 / a;
+  const R f = b / (a + b * k2);
+  const R l = lam[vec];
   const C2* ax = AX + (long long)vec * 3 * N + q;
   const C2* ox = OX + (long long)vec * 3 * N + q;
-  double rx[3], ry[3];
+  R rx[3], ry[3];
   for (int c = 0; c < 3; ++c) {
     C2 av = ax[c * N], ov = ox[c * N];
-    rx[c] = (double)av.x - l * (double)ov.x;
-    ry[c] = (double)av.y - l * (double)ov.y;
+    rx[c] = av.x - l * ov.x;
+    ry[c] = av.y - l * ov.y;
   }
-  double kx = K[0] * rx[0] + K[1] * rx[1] + K[2] * rx[2];
-  double ky = K[0] * ry[0] + K[1] * ry[1] + K[2] * ry[2];
-  for (int c = 0; c < 3; ++c)
-    w[c * N] = mk<R>((R)((rx[c] - f * K[c] * kx) / a), (R)((ry[c] - f * K[c] * ky) / a));
+  const R kx = K0 * rx[0] + K1 * rx[1] + K2 * rx[2];
+  const R ky = K0 * ry[0] + K1 * ry[1] + K2 * ry[2];
+  const R Kc[3] = {K0, K1, K2};
+  for (int c = 0; c < 3; ++c) w[c * N] = mk<R>((rx[c] - f * Kc[c] * kx) * ia, (ry[c] - f * Kc[c] * ky) * ia);
 }
 template <typename R>
 int launch_precond(const typename cplx_t<R>::type* AX, const typename cplx_t<R>::type* OX, const R* lam,

@@ -9,55 +9,86 @@
 //   small_chol -- Cholesky-QR transform T with T^H G T = I (dependent columns -> zero)
 #include "kernels.h"
 
-#define GRAM_ROWS 16
 #define GRAM_SPLIT 8
+#define GRAM_LD 73   // odd row stride of the shared tiles (columns up to 72)
 
 int g_acc64 = 0;  // experiment switch: FP64 accumulation in the FP32 Gram and update kernels
 
-
+// G_part[k][split] = A^H B over one row range.  Shared tiles are double-buffered: the next
+// tile of GRAM_ROWS rows (16 in FP32, 8 in FP64: 37 KB of static shared memory either way)
+// is fetched into registers while the current one is multiplied.
 template <typename R, typename RA>
 __global__ __launch_bounds__(256) void k_gram(BlockList<R> A, int na, BlockList<R> B, int nbk, int m, int n3,
                                               typename cplx_t<R>::type* __restrict__ part) {
   typedef typename cplx_t<R>::type C2;
   typedef typename cplx_t<RA>::type CA;
-  __shared__ C2 sA[GRAM_ROWS][72];
-  __shared__ C2 sB[GRAM_ROWS][72];
+  constexpr int GRAM_ROWS = sizeof(R) == 8 ? 8 : 16;
+  __shared__ C2 sA[2][GRAM_ROWS * GRAM_LD];
+  __shared__ C2 sB[2][GRAM_ROWS * GRAM_LD];
   const int k = blockIdx.x, split = blockIdx.y;
   const int ca = na * m, cb = nbk * m;
   const long long kofs = (long long)k * m * n3;
-  int chunk = (n3 + GRAM_SPLIT - 1) / GRAM_SPLIT;
-  int r_begin = split * chunk, r_end = min(n3, r_begin + chunk);
+  const int chunk = (n3 + GRAM_SPLIT - 1) / GRAM_SPLIT;
+  const int r_begin = split * chunk, r_end = min(n3, r_begin + chunk);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  // each thread stages elements t = threadIdx.x + 256 u of the (rows x cols) tiles
+  const int nla = (GRAM_ROWS * ca + 255) / 256, nlb = (GRAM_ROWS * cb + 255) / 256;  // <= 5 (<= 3 in FP64)
+  C2 ra[5], rb[5];
+  auto fetch = [&](int r0) {
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+      int t = threadIdx.x + 256 * u;
+      ra[u] = mk<R>(0, 0);
+      rb[u] = mk<R>(0, 0);
+      if (u < nla && t < GRAM_ROWS * ca) {
+        int rr = t % GRAM_ROWS, col = t / GRAM_ROWS, r = r0 + rr;
+        if (r < r_end) ra[u] = A.p[col / m][kofs + (long long)(col % m) * n3 + r];
+      }
+      if (u < nlb && t < GRAM_ROWS * cb) {
+        int rr = t % GRAM_ROWS, col = t / GRAM_ROWS, r = r0 + rr;
+        if (r < r_end) rb[u] = B.p[col / m][kofs + (long long)(col % m) * n3 + r];
+      }
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+      int t = threadIdx.x + 256 * u;
+      if (u < nla && t < GRAM_ROWS * ca) sA[buf][(t % GRAM_ROWS) * GRAM_LD + t / GRAM_ROWS] = ra[u];
+      if (u < nlb && t < GRAM_ROWS * cb) sB[buf][(t % GRAM_ROWS) * GRAM_LD + t / GRAM_ROWS] = rb[u];
+    }
+  };
   CA acc[5][5];
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
     for (int j = 0; j < 5; ++j) acc[i][j] = mk<RA>(0, 0);
+  int buf = 0;
+  if (r_begin < r_end) {
+    fetch(r_begin);
+    stash(0);
+  }
+  __syncthreads();
   for (int r0 = r_begin; r0 < r_end; r0 += GRAM_ROWS) {
-    for (int t = threadIdx.x; t < GRAM_ROWS * ca; t += 256) {
-      int rr = t % GRAM_ROWS, col = t / GRAM_ROWS;
-      int r = r0 + rr;
-      sA[rr][col] = (r < r_end) ? A.p[col / m][kofs + (long long)(col % m) * n3 + r] : mk<R>(0, 0);
-    }
-    for (int t = threadIdx.x; t < GRAM_ROWS * cb; t += 256) {
-      int rr = t % GRAM_ROWS, col = t / GRAM_ROWS;
-      int r = r0 + rr;
-      sB[rr][col] = (r < r_end) ? B.p[col / m][kofs + (long long)(col % m) * n3 + r] : mk<R>(0, 0);
-    }
-    __syncthreads();
+    const bool more = r0 + GRAM_ROWS < r_end;
+    if (more) fetch(r0 + GRAM_ROWS);
+    const C2* a_t = sA[buf];
+    const C2* b_t = sB[buf];
 #pragma unroll 4
     for (int rr = 0; rr < GRAM_ROWS; ++rr) {
       C2 a[5], b[5];
 #pragma unroll
-      for (int i = 0; i < 5; ++i) { int c = tx + 16 * i; a[i] = c < ca ? sA[rr][c] : mk<R>(0, 0); }
+      for (int i = 0; i < 5; ++i) { int c = tx + 16 * i; a[i] = c < ca ? a_t[rr * GRAM_LD + c] : mk<R>(0, 0); }
 #pragma unroll
-      for (int j = 0; j < 5; ++j) { int c = ty + 16 * j; b[j] = c < cb ? sB[rr][c] : mk<R>(0, 0); }
+      for (int j = 0; j < 5; ++j) { int c = ty + 16 * j; b[j] = c < cb ? b_t[rr * GRAM_LD + c] : mk<R>(0, 0); }
 #pragma unroll
       for (int i = 0; i < 5; ++i)
 #pragma unroll
         for (int j = 0; j < 5; ++j) cfmac(acc[i][j], mk<RA>(a[i].x, a[i].y), mk<RA>(b[j].x, b[j].y));
     }
+    if (more) stash(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
   C2* out = part + ((long long)k * GRAM_SPLIT + split) * ca * cb;
 #pragma unroll
@@ -237,10 +268,13 @@ __device__ void tri_inv_lower(typename cplx_t<R>::type* L, int n, int ld, typena
 
 // Two-sided cyclic Jacobi on Hermitian A (n x n, stride ld), accumulating V <- V J.  Pairs
 // are scheduled by the circle method so each round rotates n/2 disjoint planes in parallel.
-// A pair is rotated when |a_pq| > eps (sqrt(|a_pp a_qq|) + eps max|a_ii|); the iteration
-// ends after the first sweep that rotates nothing (or max_sweeps).  red: 2 blockDim entries.
+// A pair is rotated when |a_pq| > eps sqrt(|a_pp a_qq|) + eps max_{i < nx} |a_ii|, where the
+// first nx coordinates carry the current Ritz block: the absolute term is the rounding floor
+// at the scale of the wanted eigenvalues (near-zero modes would otherwise keep rotating
+// noise).  The iteration ends after the first sweep that rotates nothing (or max_sweeps).
+// red: 2 blockDim entries.
 template <typename R>
-__device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V, int n, int ld, int max_sweeps,
+__device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V, int n, int ld, int nx, int max_sweeps,
                        R* rc, typename cplx_t<R>::type* rs, int* rp, int* rq, R* red, const int* drop) {
   typedef typename cplx_t<R>::type C2;
   __shared__ int rotated;
@@ -248,7 +282,7 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
   const int npairs = npad / 2;
   const R eps = SmallEps<R>::v;
   R amax = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
+  for (int i = threadIdx.x; i < nx; i += blockDim.x)
     if (!drop[i]) amax = fmax(amax, fabs(A[i * ld + i].x));
   red[threadIdx.x] = amax;
   __syncthreads();
@@ -272,7 +306,7 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
           C2 apq = A[p * ld + q];
           R beta = sqrt(apq.x * apq.x + apq.y * apq.y);
           R app = A[p * ld + p].x, aqq = A[q * ld + q].x;
-          if (beta > eps * (sqrt(fabs(app) * fabs(aqq)) + floor_abs)) {
+          if (beta > eps * sqrt(fabs(app) * fabs(aqq)) + floor_abs) {
             R tau = (aqq - app) / (2 * beta);
             R tt = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
             c = (R)1 / sqrt((R)1 + tt * tt);
@@ -437,7 +471,7 @@ __global__ __launch_bounds__(SMALL_THREADS) void k_small_rr(const typename cplx_
     }
   }
   __syncthreads();
-  jacobi<R>(A, B, n, ld, 30, rc, rs, rp, rq, red, drop);
+  jacobi<R>(A, B, n, ld, m, 30, rc, rs, rp, rq, red, drop);
   for (int i = threadIdx.x; i < n; i += blockDim.x) ev[i] = A[i * ld + i].x;
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
