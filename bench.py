@@ -163,6 +163,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measured_peaks() -> dict:
+    """HBM copy bandwidth and bf16 GEMM throughput measured on this GPU pool (JSON at the repo root)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -275,22 +285,36 @@ def main():
     h2d = w0.rho.size * 8
     d2h = (w0.nk * w0.nbands + 1 + w0.rho.size) * 8
 
-    # ---- roofline of the dominant kernel family ----
+    # ---- roofline of each modelled kernel family; the one with the largest share is reported ----
     fp64_peak = B.pc_probe(0)
     fp32_peak = B.pc_probe(1)
-    phases = {
-        "fp64_rayleigh_ritz_gemm": (st_mx.ms_rr_gemm, st_mx.rr_gemm_flops, st_mx.rr_gemm_launches, fp64_peak, "FP64 FMA"),
-        "iteration_operator_apply": (st_mx.ms_iter_apply, st_mx.iter_apply_flops, st_mx.iter_apply_calls, fp32_peak,
-                                     "FP32 FMA"),
-    }
-    dom = max(phases, key=lambda k: phases[k][0])
-    ms_d, fl_d, n_d, peak_gf, peak_kind = phases[dom]
-    achieved = fl_d / (ms_d * 1e-3) / 1e12 if ms_d > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_gf / 1e3, "unit": "TFLOP/s",
-                "frac": achieved / (peak_gf / 1e3) if peak_gf > 0 else None, "traffic": None,
-                "peak_source": f"measured {peak_kind} throughput (pc_probe) on this GPU",
-                "launches_timed": n_d, "share_of_step": ms_d / ms_mx if ms_mx > 0 else None}
+    peaks = measured_peaks()
+    steps_ = args.steps
+    fam = {}
 
+    def add(name, ms, amount, launches, bound, peak, unit, source, traffic_key=None):
+        if ms <= 0 or peak is None:
+            return
+        achieved = amount / (ms * 1e-3) / (1e12 if unit == "TFLOP/s" else 1e9)
+        fam[name] = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak, "traffic": None, "peak_source": source,
+                     "launches_timed": int(launches), "share_of_step": ms / ms_mx}
+
+    # Gram products and basis updates (FP32 CUDA cores): FP32 FMA bound
+    add("gram_AhB", st_mx.ms_gram, st_mx.gram_flops, st_mx.gram_launches, "alu", fp32_peak / 1e3, "TFLOP/s",
+        "measured FP32 FMA throughput (pc_probe) on this GPU")
+    add("basis_update_SC", st_mx.ms_update, st_mx.update_flops, st_mx.update_launches, "alu", fp32_peak / 1e3,
+        "TFLOP/s", "measured FP32 FMA throughput (pc_probe) on this GPU")
+    # operator apply: split-BF16 tensor-core GEMM, six bf16 products per FP32-accurate product
+    if peaks.get("bf16_tflops_sustained"):
+        add("iteration_operator_apply", st_mx.ms_iter_apply, st_mx.iter_apply_flops, st_mx.iter_apply_calls, "tensor",
+            peaks["bf16_tflops_sustained"] / 6.0, "TFLOP/s",
+            "MEASURED_PEAKS.json bf16_tflops_sustained / 6 (six bf16 slice products per FP32-accurate product)")
+    add("fp64_rayleigh_ritz_gemm", st_mx.ms_rr_gemm, st_mx.rr_gemm_flops, st_mx.rr_gemm_launches, "alu",
+        fp64_peak / 1e3, "TFLOP/s", "measured FP64 FMA throughput (pc_probe) on this GPU")
+    dom = max(fam, key=lambda k: fam[k]["share_of_step"])
+    roofline = dict(fam[dom])
+    roofline["of"] = "measured"
     # ---- plain FP64 GPU form ----
     fp64 = None
     if not args.no_fp64 and args.fp64_steps > 0:
@@ -311,10 +335,17 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(st_mx.launches),
             "iterations": st_mx.iterations, "max_residual": st_mx.max_residual,
-            "phase_ms_per_step": {"rr_gemm": st_mx.ms_rr_gemm / args.steps,
+            "phase_ms_per_step": {"block_iteration": st_mx.ms_iteration_loop / args.steps,
                                   "iter_apply": st_mx.ms_iter_apply / args.steps,
+                                  "gram": st_mx.ms_gram / args.steps,
+                                  "update": st_mx.ms_update / args.steps,
                                   "small_dense": st_mx.ms_small / args.steps,
-                                  "adjoint": st_mx.ms_grad_kernels / args.steps},
+                                  "fp64_rayleigh_ritz": st_mx.ms_final_rr / args.steps,
+                                  "rr_gemm": st_mx.ms_rr_gemm / args.steps,
+                                  "adjoint": st_mx.ms_grad_kernels / args.steps,
+                                  "last_set_design": st_mx.ms_setup, "last_bands": st_mx.ms_bands,
+                                  "last_gap_and_grad": st_mx.ms_grad},
+            "roofline_families": fam,
             "fp64_form": fp64,
             "peaks_measured": {"fp64_tflops": fp64_peak / 1e3, "fp32_tflops": fp32_peak / 1e3}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == 3:

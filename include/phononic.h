@@ -84,7 +84,7 @@ typedef struct {
   int N;                   /* plane waves */
   int block;               /* block width m (bands + guard vectors) */
   double max_residual;     /* largest relative residual over the returned bands */
-  double ms_setup;         /* last pc_set_design, device time */
+  double ms_setup;         /* last pc_set_design, device time (operator assembly) */
   double ms_bands;         /* last pc_bands, device time */
   double ms_grad;          /* last pc_gap_and_grad, device time */
   long long launches;      /* kernel launches since pc_create or the last pc_clear_status */
@@ -97,6 +97,16 @@ typedef struct {
   double iter_apply_flops; /* algorithmic flops: 8 N^2 (6 + 3) per vector */
   double ms_small;         /* device time of the projected (small dense) problems */
   double ms_grad_kernels;  /* device time of the adjoint synthesis and reduction */
+  double ms_gram;          /* device time of the block iteration's Gram products A^H B */
+  long long gram_launches;
+  double gram_flops;       /* algorithmic flops: 8 rows (columns of A) (columns of B) per k */
+  double gram_bytes;       /* algorithmic bytes: both operands read once, the result written once */
+  double ms_update;        /* device time of the block iteration's basis updates S C */
+  long long update_launches;
+  double update_flops;     /* algorithmic flops: 8 rows (columns of S) (columns out) per k */
+  double update_bytes;     /* algorithmic bytes: inputs read once, outputs written once */
+  double ms_iteration_loop; /* device time of the whole block iteration (pc_bands before its FP64 step) */
+  double ms_final_rr;      /* device time of the FP64 Rayleigh-Ritz step */
 } pc_stats;
 
 /* Creates a context: validates the parameters and allocates every per-design

@@ -59,6 +59,16 @@ class pc_stats(ctypes.Structure):
         ("iter_apply_flops", ctypes.c_double),
         ("ms_small", ctypes.c_double),
         ("ms_grad_kernels", ctypes.c_double),
+        ("ms_gram", ctypes.c_double),
+        ("gram_launches", ctypes.c_longlong),
+        ("gram_flops", ctypes.c_double),
+        ("gram_bytes", ctypes.c_double),
+        ("ms_update", ctypes.c_double),
+        ("update_launches", ctypes.c_longlong),
+        ("update_flops", ctypes.c_double),
+        ("update_bytes", ctypes.c_double),
+        ("ms_iteration_loop", ctypes.c_double),
+        ("ms_final_rr", ctypes.c_double),
     ]
 
 

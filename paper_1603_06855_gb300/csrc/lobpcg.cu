@@ -272,6 +272,11 @@ __device__ void tri_inv_lower(typename cplx_t<R>::type* L, int n, int ld, typena
 // first nx coordinates carry the current Ritz block: the absolute term is the rounding floor
 // at the scale of the wanted eigenvalues (near-zero modes would otherwise keep rotating
 // noise).  The iteration ends after the first sweep that rotates nothing (or max_sweeps).
+//
+// One round is one pass over A: the planes partition the index set, so A splits into 2 x 2
+// blocks (plane t1 rows, plane t2 columns), and J^H A J maps each block to L_t1 M R_t2 on its
+// own.  Only blocks with t1 <= t2 are computed; each writes its conjugate transpose to block
+// (t2, t1), which keeps A exactly Hermitian.  The same pass rotates the column pairs of V.
 // red: 2 blockDim entries.
 template <typename R>
 __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V, int n, int ld, int nx, int max_sweeps,
@@ -281,6 +286,18 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
   const int npad = n + (n & 1);
   const int npairs = npad / 2;
   const R eps = SmallEps<R>::v;
+  // exact Hermitian start: the triangular reductions leave rounding-level asymmetry
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t / n, j = t % n;
+    if (j > i) {
+      C2 u = A[i * ld + j], l = A[j * ld + i];
+      C2 h = mk<R>((u.x + l.x) * (R)0.5, (u.y - l.y) * (R)0.5);
+      A[i * ld + j] = h;
+      A[j * ld + i] = cconj(h);
+    } else if (j == i) {
+      A[i * ld + i].y = 0;
+    }
+  }
   R amax = 0;
   for (int i = threadIdx.x; i < nx; i += blockDim.x)
     if (!drop[i]) amax = fmax(amax, fabs(A[i * ld + i].x));
@@ -292,6 +309,8 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
   }
   const R floor_abs = eps * red[0];
   __syncthreads();
+  const int nA = npairs * npairs;
+  const int nV = npairs * n;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
@@ -318,36 +337,58 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
         rp[t] = p; rq[t] = q; rc[t] = c; rs[t] = sp;
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J  (consecutive threads walk rows i of one pair)
-      for (int e = threadIdx.x; e < n * npairs; e += blockDim.x) {
-        int i = e % n, t = e / n;
-        int q = rq[t];
-        if (q >= n) continue;
-        C2 sp = rs[t];
-        if (sp.x == 0 && sp.y == 0) continue;
-        int p = rp[t];
-        R c = rc[t];
-        C2 sc = cconj(sp);
-        C2 aip = A[i * ld + p], aiq = A[i * ld + q];
-        A[i * ld + p] = csub(cscale(aip, c), cmul(sc, aiq));
-        A[i * ld + q] = cadd(cmul(sp, aip), cscale(aiq, c));
-        C2 vip = V[i * ld + p], viq = V[i * ld + q];
-        V[i * ld + p] = csub(cscale(vip, c), cmul(sc, viq));
-        V[i * ld + q] = cadd(cmul(sp, vip), cscale(viq, c));
-      }
-      __syncthreads();
-      // rows: A <- J^H A  (consecutive threads walk columns j of one pair)
-      for (int e = threadIdx.x; e < n * npairs; e += blockDim.x) {
-        int j = e % n, t = e / n;
-        int q = rq[t];
-        if (q >= n) continue;
-        C2 sp = rs[t];
-        if (sp.x == 0 && sp.y == 0) continue;
-        int p = rp[t];
-        R c = rc[t];
-        C2 apj = A[p * ld + j], aqj = A[q * ld + j];
-        A[p * ld + j] = csub(cscale(apj, c), cmul(sp, aqj));
-        A[q * ld + j] = cadd(cmul(cconj(sp), apj), cscale(aqj, c));
+      for (int e = threadIdx.x; e < nA + nV; e += blockDim.x) {
+        if (e < nA) {
+          // block (t1, t2) of A: rows p1, q1 and columns p2, q2
+          const int t1 = e / npairs, t2 = e % npairs;
+          if (t1 > t2) continue;
+          const C2 s1 = rs[t1], s2 = rs[t2];
+          const bool a1 = (s1.x != 0 || s1.y != 0), a2 = (s2.x != 0 || s2.y != 0);
+          if (!a1 && !a2) continue;
+          const R c1 = rc[t1], c2 = rc[t2];
+          const int p1 = rp[t1], q1 = rq[t1], p2 = rp[t2], q2 = rq[t2];
+          const bool v1 = q1 < n, v2 = q2 < n;
+          const C2 z = mk<R>(0, 0);
+          C2 m00 = A[p1 * ld + p2];
+          C2 m01 = v2 ? A[p1 * ld + q2] : z;
+          C2 m10 = v1 ? A[q1 * ld + p2] : z;
+          C2 m11 = (v1 && v2) ? A[q1 * ld + q2] : z;
+          // columns (plane t2): col_p <- c col_p - conj(s) col_q, col_q <- s col_p + c col_q
+          const C2 s2c = cconj(s2);
+          C2 y00 = csub(cscale(m00, c2), cmul(s2c, m01)), y01 = cadd(cmul(s2, m00), cscale(m01, c2));
+          C2 y10 = csub(cscale(m10, c2), cmul(s2c, m11)), y11 = cadd(cmul(s2, m10), cscale(m11, c2));
+          // rows (plane t1): row_p <- c row_p - s row_q, row_q <- conj(s) row_p + c row_q
+          const C2 s1c = cconj(s1);
+          m00 = csub(cscale(y00, c1), cmul(s1, y10));
+          m01 = csub(cscale(y01, c1), cmul(s1, y11));
+          m10 = cadd(cmul(s1c, y00), cscale(y10, c1));
+          m11 = cadd(cmul(s1c, y01), cscale(y11, c1));
+          if (t1 == t2) {  // the rotated plane itself: its off-diagonal pair is annihilated
+            A[p1 * ld + p1] = mk<R>(m00.x, 0);
+            if (v1) {
+              A[q1 * ld + q1] = mk<R>(m11.x, 0);
+              A[p1 * ld + q1] = z;
+              A[q1 * ld + p1] = z;
+            }
+          } else {
+            A[p1 * ld + p2] = m00;
+            A[p2 * ld + p1] = cconj(m00);
+            if (v2) { A[p1 * ld + q2] = m01; A[q2 * ld + p1] = cconj(m01); }
+            if (v1) { A[q1 * ld + p2] = m10; A[p2 * ld + q1] = cconj(m10); }
+            if (v1 && v2) { A[q1 * ld + q2] = m11; A[q2 * ld + q1] = cconj(m11); }
+          }
+        } else {
+          // row i of V, column pair t: V <- V J (consecutive threads walk rows)
+          const int e2 = e - nA;
+          const int t = e2 / n, i = e2 % n;
+          const C2 sp = rs[t];
+          if (sp.x == 0 && sp.y == 0) continue;
+          const int p = rp[t], q = rq[t];
+          const R c = rc[t];
+          const C2 vip = V[i * ld + p], viq = V[i * ld + q];
+          V[i * ld + p] = csub(cscale(vip, c), cmul(cconj(sp), viq));
+          V[i * ld + q] = cadd(cmul(sp, vip), cscale(viq, c));
+        }
       }
       __syncthreads();
     }

@@ -24,11 +24,13 @@ extern int g_acc64;     // lobpcg.cu: FP64 accumulation switch (experiments)
 long long g_pc_launches = 0;
 
 // Per-phase device timing (pc_set_profiling): event pairs recorded on the caller's stream.
-enum { PH_RR_GEMM = 0, PH_ITER_APPLY = 1, PH_SMALL = 2, PH_GRAD = 3, PH_COUNT = 4 };
+enum { PH_RR_GEMM = 0, PH_ITER_APPLY = 1, PH_SMALL = 2, PH_GRAD = 3, PH_GRAM = 4, PH_UPDATE = 5, PH_LOOP = 6,
+       PH_FINAL = 7, PH_COUNT = 8 };
 struct EventPair {
   cudaEvent_t a, b;
   int phase;
   double flops;
+  double bytes;
 };
 
 struct pc_ctx {
@@ -44,7 +46,10 @@ struct pc_ctx {
   int iterations = 0, unconv = 0;
   double max_res = 0.0;
   float ms_setup = 0.f, ms_bands = 0.f, ms_grad = 0.f;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;            // pc_bands
+  cudaEvent_t ev_s0 = nullptr, ev_s1 = nullptr;        // pc_set_design
+  cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr;        // pc_gap_and_grad
+  bool have_grad_events = false;
   int* h_unconv = nullptr;  // pinned
   // per-design (FP64)
   double *fields = nullptr, *dchi = nullptr, *chi = nullptr, *chi_mean = nullptr;
@@ -72,9 +77,10 @@ struct pc_ctx {
   int debug = 0;  // PC_DEBUG=1 prints the residual history of the block iteration to stderr
   int profiling = 0;
   std::vector<EventPair> ev_used, ev_free;
-  double ph_ms[PH_COUNT] = {0, 0, 0, 0};
-  double ph_flops[PH_COUNT] = {0, 0, 0, 0};
-  long long ph_count[PH_COUNT] = {0, 0, 0, 0};
+  double ph_ms[PH_COUNT] = {};
+  double ph_flops[PH_COUNT] = {};
+  double ph_bytes[PH_COUNT] = {};
+  long long ph_count[PH_COUNT] = {};
   long long launch_base = 0;
   unsigned long long seed = 0;  // PC_INIT_SEED: offset of the start-block perturbation
   int small32 = 1;              // projected problems of the mixed iteration in FP32 (PC_SMALL_FP32=0: FP64)
@@ -86,7 +92,7 @@ struct pc_ctx {
 };
 
 // Opens a timed phase on stream s (no-op unless profiling); returns the slot index or -1.
-static int ph_begin(pc_ctx* c, int phase, double flops, cudaStream_t s) {
+static int ph_begin(pc_ctx* c, int phase, double flops, cudaStream_t s, double bytes = 0.0) {
   if (!c->profiling) return -1;
   EventPair e;
   if (!c->ev_free.empty()) {
@@ -97,6 +103,7 @@ static int ph_begin(pc_ctx* c, int phase, double flops, cudaStream_t s) {
   }
   e.phase = phase;
   e.flops = flops;
+  e.bytes = bytes;
   cudaEventRecord(e.a, s);
   c->ev_used.push_back(e);
   return (int)c->ev_used.size() - 1;
@@ -112,6 +119,7 @@ static void ph_collect(pc_ctx* c) {
     if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
       c->ph_ms[e.phase] += ms;
       c->ph_flops[e.phase] += e.flops;
+      c->ph_bytes[e.phase] += e.bytes;
       c->ph_count[e.phase] += 1;
     }
     c->ev_free.push_back(e);
@@ -217,6 +225,8 @@ extern "C" void pc_destroy(pc_ctx* c) {
   dfree(c->Wf); dfree(c->Tf); dfree(c->status);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  for (cudaEvent_t e : {c->ev_s0, c->ev_s1, c->ev_g0, c->ev_g1})
+    if (e) cudaEventDestroy(e);
   for (auto& e : c->ev_used) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto& e : c->ev_free) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   if (c->h_unconv) cudaFreeHost(c->h_unconv);
@@ -319,6 +329,8 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
   if (rc != PC_OK) { pc_destroy(c); return PC_ENOMEM; }
   if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
       cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+      cudaEventCreate(&c->ev_s0) != cudaSuccess || cudaEventCreate(&c->ev_s1) != cudaSuccess ||
+      cudaEventCreate(&c->ev_g0) != cudaSuccess || cudaEventCreate(&c->ev_g1) != cudaSuccess ||
       cudaMallocHost((void**)&c->h_unconv, sizeof(int)) != cudaSuccess) {
     pc_destroy(c);
     return PC_ECUDA;
@@ -394,7 +406,7 @@ extern "C" int pc_set_design(pc_ctx* c, const double* rho, void* stream) {
   if (!c || !rho) return PC_EINVAL;
   cudaGetLastError();  // launch checks below report only this call's launches
   cudaStream_t s = (cudaStream_t)stream;
-  PC_CUDA_TRY(cudaEventRecord(c->ev0, s));
+  PC_CUDA_TRY(cudaEventRecord(c->ev_s0, s));
   SetupArgs a;
   a.rho = rho;
   a.n0 = c->prm.n[0]; a.n1 = c->prm.n[1]; a.n2 = c->prm.n[2];
@@ -421,7 +433,7 @@ extern "C" int pc_set_design(pc_ctx* c, const double* rho, void* stream) {
       c->tc_ready = true;
     }
   }
-  PC_CUDA_TRY(cudaEventRecord(c->ev1, s));
+  PC_CUDA_TRY(cudaEventRecord(c->ev_s1, s));
   c->have_design = true;
   c->have_bands = false;
   c->have_grad = false;
@@ -594,6 +606,30 @@ int small_chol_any<float>(pc_ctx* c, const float2* G, int m, float2* T, cudaStre
 //   W <- W T (Cholesky-QR in the Omega metric, dependent directions dropped);
 //   Rayleigh-Ritz on S = [X W P]: X <- S cX, P <- S cP (cP from the small space).
 // k-points whose wanted bands are all converged are locked.
+// Gram and update launches with their algorithmic flops and bytes recorded while profiling.
+template <typename R>
+static int gram_ph(pc_ctx* c, BlockList<R> A, int na, BlockList<R> B, int nbk, int nk, int m, int n3, R scale,
+                   typename cplx_t<R>::type* part, typename cplx_t<R>::type* G, cudaStream_t s) {
+  const double esz = sizeof(typename cplx_t<R>::type);
+  const double fl = 8.0 * n3 * (double)(na * m) * (double)(nbk * m) * nk;
+  const double by = esz * ((double)(na + nbk) * m * n3 + (double)(na * m) * (nbk * m)) * nk;
+  int sl = ph_begin(c, PH_GRAM, fl, s, by);
+  int rc = launch_gram<R>(A, na, B, nbk, nk, m, n3, scale, part, G, s);
+  ph_end(c, sl, s);
+  return rc;
+}
+template <typename R>
+static int update_ph(pc_ctx* c, const UpdateArgs<R>& u, cudaStream_t s) {
+  const double esz = sizeof(typename cplx_t<R>::type);
+  const int nsum = u.identity_last ? u.nblk - 1 : u.nblk;
+  const double fl = 8.0 * u.n3 * (double)(nsum * u.m) * u.mout * u.nk * u.ntrip;
+  const double by = esz * ((double)u.nblk * u.m + u.mout) * u.n3 * (double)u.nk * u.ntrip;
+  int sl = ph_begin(c, PH_UPDATE, fl, s, by);
+  int rc = launch_update<R>(u, s);
+  ph_end(c, sl, s);
+  return rc;
+}
+
 template <typename R>
 static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
   typedef typename Ops<R>::C2 C2;
@@ -612,13 +648,13 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
   TRY(apply_R<R>(c, X, AX, OX, s));
   {
     BlockList<R> A1 = {{X, nullptr, nullptr}}, B1 = {{AX, nullptr, nullptr}}, B2 = {{OX, nullptr, nullptr}};
-    TRY(launch_gram<R>(A1, 1, B1, 1, nk, m, n3, (R)1, part, GA, s));
-    TRY(launch_gram<R>(A1, 1, B2, 1, nk, m, n3, (R)1, part, GO, s));
+    TRY(gram_ph<R>(c, A1, 1, B1, 1, nk, m, n3, (R)1, part, GA, s));
+    TRY(gram_ph<R>(c, A1, 1, B2, 1, nk, m, n3, (R)1, part, GO, s));
     TRY(small_rr_any<R>(c, GA, GO, m, m, c->kdone, lam, Cc, nullptr, s));
     UpdateArgs<R> u = upd<R>(c, 1, 0, Cc, (long long)m * m, m, m);
     u.in[0][0] = X; u.in[1][0] = AX; u.in[2][0] = OX;
     u.out[0] = Xn; u.out[1] = AXn; u.out[2] = OXn;
-    TRY(launch_update<R>(u, s));
+    TRY(update_ph<R>(c, u, s));
     std::swap(X, Xn); std::swap(AX, AXn); std::swap(OX, OXn);
   }
   bool hasP = false;
@@ -662,13 +698,13 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
     {
       const int nproj = hasP ? 2 : 1;
       BlockList<R> A1 = {{OX, OP, nullptr}}, B1 = {{Wb, nullptr, nullptr}};
-      TRY(launch_gram<R>(A1, nproj, B1, 1, nk, m, n3, (R)-1, part, Ct, s));
+      TRY(gram_ph<R>(c, A1, nproj, B1, 1, nk, m, n3, (R)-1, part, Ct, s));
       UpdateArgs<R> u = upd<R>(c, nproj + 1, 1, Ct, (long long)nproj * m * m, m, m);
       u.ntrip = 1;
       u.in[0][0] = X;
       if (hasP) { u.in[0][1] = P; u.in[0][2] = Wb; } else { u.in[0][1] = Wb; }
       u.out[0] = Wb;
-      TRY(launch_update<R>(u, s));
+      TRY(update_ph<R>(c, u, s));
     }
     {
       int sl = ph_begin(c, PH_ITER_APPLY, 8.0 * c->N * (double)c->N * 9.0 * nk * m, s);
@@ -678,21 +714,21 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
     // W <- W T with T^H (W^H Omega W) T = I, dependent directions dropped
     {
       BlockList<R> A1 = {{Wb, nullptr, nullptr}}, B1 = {{OW, nullptr, nullptr}};
-      TRY(launch_gram<R>(A1, 1, B1, 1, nk, m, n3, (R)1, part, GO, s));
+      TRY(gram_ph<R>(c, A1, 1, B1, 1, nk, m, n3, (R)1, part, GO, s));
       int sl = ph_begin(c, PH_SMALL, 0.0, s);
       TRY(small_chol_any<R>(c, GO, m, Cc, s));
       ph_end(c, sl, s);
       UpdateArgs<R> u = upd<R>(c, 1, 0, Cc, (long long)m * m, m, m);
       u.in[0][0] = Wb; u.in[1][0] = AW; u.in[2][0] = OW;
       u.out[0] = Wb; u.out[1] = AW; u.out[2] = OW;
-      TRY(launch_update<R>(u, s));
+      TRY(update_ph<R>(c, u, s));
     }
     // Rayleigh-Ritz on S = [X W P]
     const int ns = hasP ? 3 : 2;
     const int n = ns * m;
     BlockList<R> S1 = {{X, Wb, P}}, SA = {{AX, AW, AP}}, SO = {{OX, OW, OP}};
-    TRY(launch_gram<R>(S1, ns, SA, ns, nk, m, n3, (R)1, part, GA, s));
-    TRY(launch_gram<R>(S1, ns, SO, ns, nk, m, n3, (R)1, part, GO, s));
+    TRY(gram_ph<R>(c, S1, ns, SA, ns, nk, m, n3, (R)1, part, GA, s));
+    TRY(gram_ph<R>(c, S1, ns, SO, ns, nk, m, n3, (R)1, part, GO, s));
     {
       int sl = ph_begin(c, PH_SMALL, 0.0, s);
       TRY(small_rr_any<R>(c, GA, GO, n, m, c->kdone, lam, Cc, Ct, s));
@@ -704,11 +740,11 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
       u.in[1][0] = AX; u.in[1][1] = AW; u.in[1][2] = AP;
       u.in[2][0] = OX; u.in[2][1] = OW; u.in[2][2] = OP;
       u.out[0] = Xn; u.out[1] = AXn; u.out[2] = OXn;
-      TRY(launch_update<R>(u, s));
+      TRY(update_ph<R>(c, u, s));
       UpdateArgs<R> v = u;
       v.C = Ct;
       v.out[0] = Pn; v.out[1] = APn; v.out[2] = OPn;
-      TRY(launch_update<R>(v, s));
+      TRY(update_ph<R>(c, v, s));
     }
     std::swap(X, Xn); std::swap(AX, AXn); std::swap(OX, OXn);
     std::swap(P, Pn); std::swap(AP, APn); std::swap(OP, OPn);
@@ -784,9 +820,13 @@ extern "C" int pc_bands(pc_ctx* c, double* omega, void* stream) {
   if (!c->have_design || c->nk == 0) return PC_ESTATE;
   cudaStream_t s = (cudaStream_t)stream;
   PC_CUDA_TRY(cudaEventRecord(c->ev0, s));
+  int sl = ph_begin(c, PH_LOOP, 0.0, s);
   int rc = (c->prm.precision == PC_FP64) ? run_block_iteration<double>(c, s) : run_block_iteration<float>(c, s);
+  ph_end(c, sl, s);
   if (rc) return rc;
+  sl = ph_begin(c, PH_FINAL, 0.0, s);
   rc = fp64_rayleigh_ritz(c, s);
+  ph_end(c, sl, s);
   if (rc) return rc;
   rc = launch_omega(c->lamd, c->nk, c->nb, c->m, c->lref, omega, c->lam_nd, s);
   if (rc) return rc;
@@ -805,7 +845,7 @@ extern "C" int pc_gap_and_grad(pc_ctx* c, int n_lower, int mode, const double* w
   if (!c->have_bands) return PC_ESTATE;
   cudaGetLastError();  // launch checks below report only this call's launches
   cudaStream_t s = (cudaStream_t)stream;
-  PC_CUDA_TRY(cudaEventRecord(c->ev0, s));
+  PC_CUDA_TRY(cudaEventRecord(c->ev_g0, s));
   GapArgs g;
   g.lam = c->lam_nd;
   g.nk = c->nk; g.nb = c->nb; g.n_lower = n_lower; g.mode = mode;
@@ -844,7 +884,8 @@ extern "C" int pc_gap_and_grad(pc_ctx* c, int n_lower, int mode, const double* w
     ph_end(c, sl, s);
     if (rc) return rc;
   }
-  PC_CUDA_TRY(cudaEventRecord(c->ev1, s));
+  PC_CUDA_TRY(cudaEventRecord(c->ev_g1, s));
+  c->have_grad_events = true;
   c->have_grad = true;
   return PC_OK;
 }
@@ -874,7 +915,9 @@ extern "C" int pc_get_stats(pc_ctx* c, pc_stats* out) {
   }
   if (st == PC_OK && c->unconv > 0) st = PC_ENOCONV;
   float ms = 0;
-  if (c->have_design && cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) out->ms_bands = ms;
+  if (c->have_design && cudaEventElapsedTime(&ms, c->ev_s0, c->ev_s1) == cudaSuccess) out->ms_setup = ms;
+  if (c->have_bands && cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) out->ms_bands = ms;
+  if (c->have_grad_events && cudaEventElapsedTime(&ms, c->ev_g0, c->ev_g1) == cudaSuccess) out->ms_grad = ms;
   cudaGetLastError();  // a query on events of an unfinished call must not leak into later launch checks
   out->launches = g_pc_launches - c->launch_base;
   ph_collect(c);
@@ -886,6 +929,16 @@ extern "C" int pc_get_stats(pc_ctx* c, pc_stats* out) {
   out->iter_apply_flops = c->ph_flops[PH_ITER_APPLY];
   out->ms_small = c->ph_ms[PH_SMALL];
   out->ms_grad_kernels = c->ph_ms[PH_GRAD];
+  out->ms_gram = c->ph_ms[PH_GRAM];
+  out->gram_launches = c->ph_count[PH_GRAM];
+  out->gram_flops = c->ph_flops[PH_GRAM];
+  out->gram_bytes = c->ph_bytes[PH_GRAM];
+  out->ms_update = c->ph_ms[PH_UPDATE];
+  out->update_launches = c->ph_count[PH_UPDATE];
+  out->update_flops = c->ph_flops[PH_UPDATE];
+  out->update_bytes = c->ph_bytes[PH_UPDATE];
+  out->ms_iteration_loop = c->ph_ms[PH_LOOP];
+  out->ms_final_rr = c->ph_ms[PH_FINAL];
   out->status = st;
   return st;
 }
@@ -901,7 +954,7 @@ extern "C" int pc_set_profiling(pc_ctx* c, int on) {
   if (!c) return PC_EINVAL;
   PC_CUDA_TRY(cudaDeviceSynchronize());
   ph_collect(c);
-  for (int i = 0; i < PH_COUNT; ++i) { c->ph_ms[i] = 0; c->ph_flops[i] = 0; c->ph_count[i] = 0; }
+  for (int i = 0; i < PH_COUNT; ++i) { c->ph_ms[i] = 0; c->ph_flops[i] = 0; c->ph_bytes[i] = 0; c->ph_count[i] = 0; }
   c->profiling = on ? 1 : 0;
   return PC_OK;
 }
