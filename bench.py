@@ -300,11 +300,13 @@ def main():
                      "frac": achieved / peak, "traffic": None, "peak_source": source,
                      "launches_timed": int(launches), "share_of_step": ms / ms_mx}
 
-    # Gram products and basis updates (FP32 CUDA cores): FP32 FMA bound
-    add("gram_AhB", st_mx.ms_gram, st_mx.gram_flops, st_mx.gram_launches, "alu", fp32_peak / 1e3, "TFLOP/s",
-        "measured FP32 FMA throughput (pc_probe) on this GPU")
-    add("basis_update_SC", st_mx.ms_update, st_mx.update_flops, st_mx.update_launches, "alu", fp32_peak / 1e3,
-        "TFLOP/s", "measured FP32 FMA throughput (pc_probe) on this GPU")
+    # Gram products and basis updates: split-BF16 tensor-core kernels that read each FP32 operand
+    # once and write the result once, so HBM bound (algorithmic bytes / measured copy bandwidth)
+    if peaks.get("hbm_gbs"):
+        add("gram_AhB", st_mx.ms_gram, st_mx.gram_bytes, st_mx.gram_launches, "hbm", peaks["hbm_gbs"], "GB/s",
+            "MEASURED_PEAKS.json hbm_gbs")
+        add("basis_update_SC", st_mx.ms_update, st_mx.update_bytes, st_mx.update_launches, "hbm", peaks["hbm_gbs"],
+            "GB/s", "MEASURED_PEAKS.json hbm_gbs")
     # operator apply: split-BF16 tensor-core GEMM, six bf16 products per FP32-accurate product
     if peaks.get("bf16_tflops_sustained"):
         add("iteration_operator_apply", st_mx.ms_iter_apply, st_mx.iter_apply_flops, st_mx.iter_apply_calls, "tensor",
@@ -326,7 +328,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64 (FP32 block iteration, FP64 projected problems and Rayleigh-Ritz)",
+            "vs_baseline": None, "dtype": "f32 block iteration (split-bf16x3 tensor-core contractions, f32 projected problems) + f64 Rayleigh-Ritz",
             "data": "synthetic",
             "config": {"workload": WORKLOAD if args.config == 3 else ws[0].name, "designs_per_step": 1, "k_per_design": w0.nk, "bands": w0.nbands,
                        "adjoint": "all-band weighted (every (k, band))",

@@ -198,6 +198,16 @@ int pc_export(pc_ctx* ctx, int which, double* host, long long capacity, long lon
 int pc_apply_operator(pc_ctx* ctx, int k, int ncols, const double* x_dev,
                       double* ax_dev, double* ox_dev, void* stream);
 
+/* Self-check of the tensor-core kernels of the FP32 block iteration (synchronous; allocates
+ * and frees its own scratch).  On seeded data with columns of norms spread over 2^-3..2^3,
+ * what = 0 runs the batched Gram product G = A^H B (nblk blocks of m columns per side, n3
+ * rows, nk problems) and what = 1 the basis update out = [S] C with two coefficient sets,
+ * three operand triplets and an identity last block (nblk > 1), once on the split-BF16
+ * tensor cores and once on the FP32 CUDA cores; *rel_err = max |difference| / max |CUDA-core
+ * result|.  Not on the hot path.  Errors: PC_EINVAL (m > 24, nblk > 3, bad what or sizes),
+ * PC_ENOMEM, PC_ECUDA, PC_ETIMEOUT (a bounded wait of a tensor-core kernel expired). */
+int pc_check_tensor_kernels(int what, int nk, int m, int nblk, int n3, double* rel_err);
+
 /* --- Allocation-free entry point (no counterpart in the paper) ---
  *
  * For callers that may not allocate device memory once they are running: processes that

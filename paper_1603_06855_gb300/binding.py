@@ -74,7 +74,7 @@ class pc_stats(ctypes.Structure):
 
 EXPORTED = ["pc_create", "pc_set_kpoints", "pc_set_design", "pc_bands", "pc_gap_and_grad", "pc_get_stats",
             "pc_clear_status", "pc_set_profiling", "pc_probe", "pc_destroy", "pc_strerror", "pc_export",
-            "pc_apply_operator", "pc_structure_factors_noalloc"]
+            "pc_apply_operator", "pc_check_tensor_kernels", "pc_structure_factors_noalloc"]
 
 _lib = None
 
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
     lib.pc_export.argtypes = [P, I, P, LL, ctypes.POINTER(LL)]
     lib.pc_apply_operator.argtypes = [P, I, I, P, P, P, P]
     lib.pc_structure_factors_noalloc.argtypes = [ctypes.POINTER(pc_params), P, P, P]
+    lib.pc_check_tensor_kernels.argtypes = [I, I, I, I, I, ctypes.POINTER(ctypes.c_double)]
     for name in EXPORTED:
         if name not in ("pc_destroy", "pc_strerror"):
             getattr(lib, name).restype = I
@@ -213,6 +214,13 @@ def pc_export(ctx: int, which: int):
 
 def pc_apply_operator(ctx: int, k: int, ncols: int, x_ptr: int, ax_ptr: int, ox_ptr: int, stream: int = 0):
     _check(load().pc_apply_operator(ctx, k, ncols, x_ptr, ax_ptr, ox_ptr, stream), "pc_apply_operator")
+
+
+def pc_check_tensor_kernels(what: int, nk: int, m: int, nblk: int, n3: int) -> float:
+    """Tensor-core vs CUDA-core Gram (what=0) or basis update (what=1): max relative difference."""
+    err = ctypes.c_double(-1.0)
+    _check(load().pc_check_tensor_kernels(what, nk, m, nblk, n3, ctypes.byref(err)), "pc_check_tensor_kernels")
+    return err.value
 
 
 def pc_structure_factors_noalloc(params: pc_params, rho_ptr: int, sfac_ptr: int, stream: int = 0) -> int:

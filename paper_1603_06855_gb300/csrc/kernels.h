@@ -79,7 +79,7 @@ template <typename R> struct BlockList {
 };
 template <typename R>
 int launch_gram(BlockList<R> A, int na, BlockList<R> B, int nb_, int nk, int m, int n3, R scale,
-                typename cplx_t<R>::type* part, typename cplx_t<R>::type* G, cudaStream_t s);
+                typename cplx_t<R>::type* part, typename cplx_t<R>::type* G, cudaStream_t s, int* status = nullptr);
 template <typename R> struct UpdateArgs {
   const typename cplx_t<R>::type* in[3][3];  // [triplet][block]
   typename cplx_t<R>::type* out[3];
@@ -90,8 +90,17 @@ template <typename R> struct UpdateArgs {
   int cld;             // leading dimension (columns) of C
   int m, mout, n3, nk;
   long long in_kstride, out_kstride;  // elements per k (normally m*n3 / mout*n3)
+  // optional second coefficient set over the same inputs: out2[t] = sum_b in[t][b] C2nd_b
+  const typename cplx_t<R>::type* C2nd = nullptr;
+  typename cplx_t<R>::type* out2[3] = {nullptr, nullptr, nullptr};
+  int* status = nullptr;  // device status word (tensor-core kernels record a timeout there)
 };
 template <typename R> int launch_update(const UpdateArgs<R>& a, cudaStream_t s);
+// Tensor-core versions for FP32 data (tall_tc.cu); g_tc_tall = 0 selects the CUDA-core kernels.
+extern int g_tc_tall;
+int launch_gram_tc(const float2* const A[3], int na, const float2* const B[3], int nbk, int nk, int m, int n3,
+                   float scale, float2* part, int max_split, float2* G, int* status, cudaStream_t s);
+int launch_update_tc(const UpdateArgs<float>& u, int* status, cudaStream_t s);
 
 template <typename R>
 int launch_small_rr(const typename cplx_t<R>::type* GA, const typename cplx_t<R>::type* GO, int n, int m,

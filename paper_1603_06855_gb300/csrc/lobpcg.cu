@@ -7,6 +7,7 @@
 //                 drops dependent columns, reduction to standard form, cyclic Jacobi,
 //                 lowest m Ritz pairs
 //   small_chol -- Cholesky-QR transform T with T^H G T = I (dependent columns -> zero)
+#include <type_traits>
 #include "kernels.h"
 
 #define GRAM_SPLIT 8
@@ -101,34 +102,44 @@ __global__ __launch_bounds__(256) void k_gram(BlockList<R> A, int na, BlockList<
 }
 
 template <typename R>
-__global__ void k_gram_reduce(const typename cplx_t<R>::type* __restrict__ part, int nel, R scale,
+__global__ void k_gram_reduce(const typename cplx_t<R>::type* __restrict__ part, int nsplit, int nel, R scale,
                               typename cplx_t<R>::type* __restrict__ G) {
   typedef typename cplx_t<R>::type C2;
   int k = blockIdx.y;
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nel) return;
-  const C2* p = part + (long long)k * GRAM_SPLIT * nel + e;
+  const C2* p = part + (long long)k * nsplit * nel + e;
   C2 s = mk<R>(0, 0);
-  for (int i = 0; i < GRAM_SPLIT; ++i) s = cadd(s, p[(long long)i * nel]);
+  for (int i = 0; i < nsplit; ++i) s = cadd(s, p[(long long)i * nel]);
   G[(long long)k * nel + e] = cscale(s, scale);
+}
+
+int launch_gram_reduce_f(const float2* part, int nsplit, int nel, int nk, float scale, float2* G, cudaStream_t s) {
+  dim3 g2(cdiv(nel, 256), nk);
+  k_gram_reduce<float><<<g2, 256, 0, s>>>(part, nsplit, nel, scale, G);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
 }
 
 template <typename R>
 int launch_gram(BlockList<R> A, int na, BlockList<R> B, int nbk, int nk, int m, int n3, R scale,
-                typename cplx_t<R>::type* part, typename cplx_t<R>::type* G, cudaStream_t s) {
+                typename cplx_t<R>::type* part, typename cplx_t<R>::type* G, cudaStream_t s, int* status) {
   if (na * m > 72 || nbk * m > 72 || na * m > 80) return PC_EINVAL;
+  if constexpr (std::is_same<R, float>::value) {
+    if (g_tc_tall && status && !g_acc64) return launch_gram_tc(A.p, na, B.p, nbk, nk, m, n3, scale, part, GRAM_SPLIT, G, status, s);
+  }
   dim3 grid(nk, GRAM_SPLIT);
   if (g_acc64) k_gram<R, double><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
   else k_gram<R, R><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
   PC_LAUNCH_CHECK();
   int nel = na * m * nbk * m;
   dim3 g2(cdiv(nel, 256), nk);
-  k_gram_reduce<R><<<g2, 256, 0, s>>>(part, nel, scale, G);
+  k_gram_reduce<R><<<g2, 256, 0, s>>>(part, GRAM_SPLIT, nel, scale, G);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
-template int launch_gram<double>(BlockList<double>, int, BlockList<double>, int, int, int, int, double, double2*, double2*, cudaStream_t);
-template int launch_gram<float>(BlockList<float>, int, BlockList<float>, int, int, int, int, float, float2*, float2*, cudaStream_t);
+template int launch_gram<double>(BlockList<double>, int, BlockList<double>, int, int, int, int, double, double2*, double2*, cudaStream_t, int*);
+template int launch_gram<float>(BlockList<float>, int, BlockList<float>, int, int, int, int, float, float2*, float2*, cudaStream_t, int*);
 
 // ---------------------------------------------------------------------------
 // out[t][k][j][r] = (identity_last ? in[t][last][k][j][r] : 0) + sum_b sum_i in[t][b][k][i][r] C[k][b*m+i][j]
@@ -176,7 +187,7 @@ __global__ __launch_bounds__(128) void k_update(UpdateArgs<R> a) {
     if (j < a.mout) dst[(long long)j * a.n3] = mk<R>((R)acc[j].x, (R)acc[j].y);
 }
 
-template <typename R> int launch_update(const UpdateArgs<R>& a, cudaStream_t s) {
+template <typename R> static int launch_update_cuda(const UpdateArgs<R>& a, cudaStream_t s) {
   int nsum = a.identity_last ? a.nblk - 1 : a.nblk;
   if (nsum * a.m * a.mout > 72 * 24 || a.mout > 24) return PC_EINVAL;
   dim3 grid(cdiv(a.n3, 128), a.nk, a.ntrip);
@@ -191,6 +202,21 @@ template <typename R> int launch_update(const UpdateArgs<R>& a, cudaStream_t s) 
   }
   PC_LAUNCH_CHECK();
   return PC_OK;
+}
+
+// out[t] = [in] C (and out2[t] = [in] C2nd when a second coefficient set is given).  The CUDA-core
+// kernel takes one set per launch; the tensor-core kernel (FP32) takes both in one pass.
+template <typename R> int launch_update(const UpdateArgs<R>& a, cudaStream_t s) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (g_tc_tall && a.status && !g_acc64) return launch_update_tc(a, a.status, s);
+  }
+  int rc = launch_update_cuda<R>(a, s);
+  if (rc || !a.C2nd) return rc;
+  UpdateArgs<R> b = a;
+  b.C = a.C2nd;
+  for (int t = 0; t < 3; ++t) b.out[t] = a.out2[t];
+  b.C2nd = nullptr;
+  return launch_update_cuda<R>(b, s);
 }
 template int launch_update<double>(const UpdateArgs<double>&, cudaStream_t);
 template int launch_update<float>(const UpdateArgs<float>&, cudaStream_t);

@@ -259,7 +259,6 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
     const char* dbg = getenv("PC_DEBUG");
     c->debug = (dbg && dbg[0] == '1') ? 1 : 0;
     const char* acc = getenv("PC_ACC64");
-    
     g_acc64 = (acc && acc[0] == '1') ? 1 : 0;
     const char* rf = getenv("PC_REFRESH");
     if (rf && atoi(rf) > 0) c->refresh = atoi(rf);
@@ -271,7 +270,8 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
     c->small32 = (s32 && s32[0] == '0') ? 0 : 1;
     const char* sd = getenv("PC_INIT_SEED");
     c->seed = sd ? strtoull(sd, nullptr, 10) : 0ull;
-
+    const char* tt = getenv("PC_TC_TALL");
+    g_tc_tall = (tt && tt[0] == '0') ? 0 : 1;
   }
   if (c->prm.tol == 0) c->prm.tol = (p->precision == PC_FP64) ? 1e-8 : 1e-4;
   if (c->prm.max_iter == 0) c->prm.max_iter = (p->precision == PC_FP64) ? 600 : 400;
@@ -542,6 +542,7 @@ static UpdateArgs<R> upd(pc_ctx* c, int nblk, int identity_last, const void* Cma
   u.in_kstride = (long long)c->m * 3 * c->N;
   u.out_kstride = (long long)mout * 3 * c->N;
   u.ntrip = 3;
+  u.status = c->status;
   return u;
 }
 
@@ -614,7 +615,7 @@ static int gram_ph(pc_ctx* c, BlockList<R> A, int na, BlockList<R> B, int nbk, i
   const double fl = 8.0 * n3 * (double)(na * m) * (double)(nbk * m) * nk;
   const double by = esz * ((double)(na + nbk) * m * n3 + (double)(na * m) * (nbk * m)) * nk;
   int sl = ph_begin(c, PH_GRAM, fl, s, by);
-  int rc = launch_gram<R>(A, na, B, nbk, nk, m, n3, scale, part, G, s);
+  int rc = launch_gram<R>(A, na, B, nbk, nk, m, n3, scale, part, G, s, c->status);
   ph_end(c, sl, s);
   return rc;
 }
@@ -622,8 +623,9 @@ template <typename R>
 static int update_ph(pc_ctx* c, const UpdateArgs<R>& u, cudaStream_t s) {
   const double esz = sizeof(typename cplx_t<R>::type);
   const int nsum = u.identity_last ? u.nblk - 1 : u.nblk;
-  const double fl = 8.0 * u.n3 * (double)(nsum * u.m) * u.mout * u.nk * u.ntrip;
-  const double by = esz * ((double)u.nblk * u.m + u.mout) * u.n3 * (double)u.nk * u.ntrip;
+  const int nset = u.C2nd ? 2 : 1;
+  const double fl = 8.0 * u.n3 * (double)(nsum * u.m) * u.mout * nset * u.nk * u.ntrip;
+  const double by = esz * ((double)u.nblk * u.m + (double)nset * u.mout) * u.n3 * (double)u.nk * u.ntrip;
   int sl = ph_begin(c, PH_UPDATE, fl, s, by);
   int rc = launch_update<R>(u, s);
   ph_end(c, sl, s);
@@ -740,11 +742,9 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
       u.in[1][0] = AX; u.in[1][1] = AW; u.in[1][2] = AP;
       u.in[2][0] = OX; u.in[2][1] = OW; u.in[2][2] = OP;
       u.out[0] = Xn; u.out[1] = AXn; u.out[2] = OXn;
+      u.C2nd = Ct;  // conjugate directions from the same inputs
+      u.out2[0] = Pn; u.out2[1] = APn; u.out2[2] = OPn;
       TRY(update_ph<R>(c, u, s));
-      UpdateArgs<R> v = u;
-      v.C = Ct;
-      v.out[0] = Pn; v.out[1] = APn; v.out[2] = OPn;
-      TRY(update_ph<R>(c, v, s));
     }
     std::swap(X, Xn); std::swap(AX, AXn); std::swap(OX, OXn);
     std::swap(P, Pn); std::swap(AP, APn); std::swap(OP, OPn);

@@ -1,0 +1,40 @@
+"""Tensor-core kernels of the FP32 block iteration against the FP32 CUDA-core kernels.
+
+The batched Gram product A^H B and the basis update [S] C run on tcgen05 with both operands
+split into three bf16 slices (six slice products, FP32 accumulation in tensor memory).  On
+seeded data with column norms spread over 2^-3..2^3 they must agree with the CUDA-core FP32
+kernels to 2e-5 of the largest result entry: both keep about 24 significant bits per operand
+and accumulate in FP32, so the difference is a few FP32 roundings of sums of up to 4374 terms.
+Sizes cover several 32-row stages and 128-row tiles with ragged tails, fewer rows than one
+stage, block widths that are not multiples of 16, and one to three blocks per side.
+"""
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_06855_gb300 import binding, build_lib
+    build_lib.build()
+    binding.load()
+    return binding
+
+
+@pytest.mark.parametrize("nk,m,nblk,n3", [(3, 24, 3, 2187), (5, 10, 2, 75), (2, 16, 1, 33), (7, 24, 1, 1029),
+                                          (150, 24, 3, 375)])
+def test_gram_tensor_cores(B, nk, m, nblk, n3):
+    err = B.pc_check_tensor_kernels(0, nk, m, nblk, n3)
+    assert 0 <= err < TOL, err
+
+
+@pytest.mark.parametrize("nk,m,nblk,n3", [(3, 24, 3, 2187), (5, 10, 2, 75), (2, 16, 1, 33), (4, 20, 3, 1029),
+                                          (150, 24, 3, 375), (6, 8, 3, 130)])
+def test_update_tensor_cores(B, nk, m, nblk, n3):
+    err = B.pc_check_tensor_kernels(1, nk, m, nblk, n3)
+    assert 0 <= err < TOL, err
