@@ -8,8 +8,8 @@
 // real vector (Re s_i, Im s_i)_i and each output column is two real columns of coefficients,
 // (Re c, -Im c) for the real part and (Im c, Re c) for the imaginary part.
 //
-// The FP32 operands are split into three bf16 slices in shared memory by the staging warps
-// (x = hi + mid + lo, about 24 significant bits); the six slice products of order at most 2^-16
+// The FP32 operands are split exactly into three bf16 slices in shared memory by the staging
+// warps (x = hi + mid + lo, 8 significand bits each); the six slice products of order at most 2^-16
 // (hh, hm, mh, hl, mm, lh) are accumulated in FP32 in tensor memory by tcgen05.mma
 // (kind::f16, M = 128, K = 16).  Staging is double-buffered against the MMAs with mbarriers;
 // every wait is bounded and records PC_ETIMEOUT in the status word when it expires.
@@ -57,8 +57,9 @@ __device__ __forceinline__ uint32_t rot_pair(uint32_t w) { return __funnelshift_
 
 // ---------------------------------------------------------------------------
 // Gram products.
-constexpr int G_THREADS = 288;  // warps 0-7 stage operands (warps 0-3 also drain), warp 8 issues MMAs
-constexpr int G_PRODUCERS = 256;
+constexpr int G_THREADS = 544;  // warps 0-15 stage operands (warps 0-3 also drain), warp 16 issues MMAs
+constexpr int G_PRODUCERS = 512;
+constexpr int G_MMA_WARP = 16;
 constexpr int G_BROWS = 144;    // B rows: cb real parts + cb rotated parts, cb <= 72
 constexpr int G_B_SLICE = G_BROWS * 128;
 constexpr int G_STAGE = 3 * (A_SLICE + G_B_SLICE);
@@ -98,7 +99,7 @@ __global__ __launch_bounds__(G_THREADS, 1) void k_tc_gram(TcGramArgs a) {
     mbar_init(bars + 32, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) {
+  if (warp == G_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(256u)
                  : "memory");
@@ -109,7 +110,7 @@ __global__ __launch_bounds__(G_THREADS, 1) void k_tc_gram(TcGramArgs a) {
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp < 8) {
+  if (warp < G_MMA_WARP) {
     // Every load of a stage is issued before any is used, and the loads of stage it + 1 are
     // in flight while stage it is split and stored: one HBM latency per stage, overlapped.
     const int nitems = (ca + cb) * 16;
@@ -145,7 +146,7 @@ __global__ __launch_bounds__(G_THREADS, 1) void k_tc_gram(TcGramArgs a) {
         if (e < nitems) {
           const int c = e >> 4, q = e & 15;
           uint2 h, mi, lo;
-          split4_bf16(x0[u].x, x0[u].y, x1[u].x, x1[u].y, h, mi, lo);
+          split4_exact(x0[u].x, x0[u].y, x1[u].x, x1[u].y, h, mi, lo);
           if (c < ca) {
             const uint32_t off = sw128_offset(c, 8 * q);
             *reinterpret_cast<uint2*>(stp + off) = h;
@@ -226,7 +227,7 @@ __global__ __launch_bounds__(G_THREADS, 1) void k_tc_gram(TcGramArgs a) {
     const int i = e / cb, j = e % cb;
     out[e] = make_float2(stage[i * ld + j], stage[i * ld + cb + j]);
   }
-  if (warp == 8) {
+  if (warp == G_MMA_WARP) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
   }
@@ -234,8 +235,9 @@ __global__ __launch_bounds__(G_THREADS, 1) void k_tc_gram(TcGramArgs a) {
 
 // ---------------------------------------------------------------------------
 // Basis updates.
-constexpr int U_THREADS = 416;  // warps 0-7 stage, warps 8-11 drain, warp 12 issues MMAs
-constexpr int U_PRODUCERS = 256;
+constexpr int U_THREADS = 672;  // warps 0-15 stage, warps 16-19 drain, warp 20 issues MMAs
+constexpr int U_PRODUCERS = 512;
+constexpr int U_EPI_WARP = 16, U_MMA_WARP = 20;
 constexpr int U_EPI = 128;
 constexpr int U_KMAX = 192;     // padded real K (2 * 72 input columns -> 144 -> 3 atoms)
 constexpr int U_NMAX = 96;
@@ -285,7 +287,7 @@ __global__ __launch_bounds__(U_THREADS, 1) void k_tc_update(TcUpdateArgs a) {
     mbar_init(bars + 64, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 12) {
+  if (warp == U_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(256u)
                  : "memory");
@@ -328,14 +330,10 @@ __global__ __launch_bounds__(U_THREADS, 1) void k_tc_update(TcUpdateArgs a) {
         if (part == 0) { x0 = c.x; x1 = -c.y; }
         else { x0 = c.y; x1 = c.x; }
       }
-      __nv_bfloat16 h0, m0, l0, h1, m1, l1;
-      split3_bf16(x0, h0, m0, l0);
-      split3_bf16(x1, h1, m1, l1);
+      uint32_t w[3];
+      split2_exact(x0, x1, w[0], w[1], w[2]);
       const int at = i >> 5;                 // atom of K = 2i
       const uint32_t off = sw128_offset(jj, 4 * (i & 31));
-      const uint32_t w[3] = {(uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16),
-                             (uint32_t)__bfloat16_as_ushort(m0) | ((uint32_t)__bfloat16_as_ushort(m1) << 16),
-                             (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16)};
 #pragma unroll
       for (int sl = 0; sl < 3; ++sl)
         *reinterpret_cast<uint32_t*>(gbase + (size_t)(sl * nat + at) * NP * 128 + off) = w[sl];
@@ -348,7 +346,7 @@ __global__ __launch_bounds__(U_THREADS, 1) void k_tc_update(TcUpdateArgs a) {
   const uint32_t tmem = *tmem_slot;
   const int nstage = ntl * nat;
 
-  if (warp < 8) {
+  if (warp < U_EPI_WARP) {
     // All loads of a stage are issued together; the next stage's loads are in flight while
     // the current one is split and stored.
     float2 pa[2][U_MAXI], pb[2][U_MAXI];
@@ -388,7 +386,7 @@ __global__ __launch_bounds__(U_THREADS, 1) void k_tc_update(TcUpdateArgs a) {
         const int rr = e & 127, ip = e >> 7;
         if (ip < nip) {
           uint2 h, mi, lo;
-          split4_bf16(x0[u].x, x0[u].y, x1[u].x, x1[u].y, h, mi, lo);
+          split4_exact(x0[u].x, x0[u].y, x1[u].x, x1[u].y, h, mi, lo);
           const uint32_t off = sw128_offset(rr, 8 * ip);
           *reinterpret_cast<uint2*>(stp + off) = h;
           *reinterpret_cast<uint2*>(stp + A_SLICE + off) = mi;
@@ -410,7 +408,7 @@ __global__ __launch_bounds__(U_THREADS, 1) void k_tc_update(TcUpdateArgs a) {
       fence_async_smem();
       mbar_arrive(bars + 8);
     }
-  } else if (warp < 12) {
+  } else if (warp < U_MMA_WARP) {
     const int quad = warp & 3;
     const int r_in = quad * 32 + lane;
     for (int tl = 0; tl < ntl; ++tl) {
@@ -418,23 +416,25 @@ __global__ __launch_bounds__(U_THREADS, 1) void k_tc_update(TcUpdateArgs a) {
       const uint32_t ph = (uint32_t)(tl >> 1) & 1u;
       const bool ok = __all_sync(0xffffffffu, mbar_wait(bars + 32 + 8 * b, ph, a.status));
       tc_fence_after();
-      float v[NP];
-#pragma unroll
-      for (int c0 = 0; c0 < NP; c0 += 16)
-        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 128 + c0), v + c0);
-      tc_fence_before();
-      mbar_arrive(bars + 48 + 8 * b);
-      if (!ok) break;
       const int r = (tile0 + tl) * 128 + r_in;
-      if (r < a.n3) {
 #pragma unroll
-        for (int h = 0; h < NC; ++h) {
+      for (int h = 0; h < NC; ++h) {
+        // columns h * 2 MOUT .. + 2 MOUT: real parts, then imaginary parts, of set h
+        constexpr int NW = ((2 * MOUT + 15) / 16) * 16;
+        float v[NW];
+#pragma unroll
+        for (int c0 = 0; c0 < NW; c0 += 16)
+          tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 128 + h * 2 * MOUT + c0), v + c0);
+        if (ok && r < a.n3) {
           float2* dst = a.out[h][t] + (long long)k * a.out_kstride + r;
 #pragma unroll
           for (int j = 0; j < MOUT; ++j)
-            if (j < a.mout) dst[(long long)j * a.n3] = make_float2(v[h * 2 * MOUT + j], v[h * 2 * MOUT + MOUT + j]);
+            if (j < a.mout) dst[(long long)j * a.n3] = make_float2(v[j], v[MOUT + j]);
         }
       }
+      tc_fence_before();
+      mbar_arrive(bars + 48 + 8 * b);
+      if (!ok) break;
     }
   } else if (lane == 0) {
     const uint32_t idesc = idesc_bf16_n(NP);
@@ -475,7 +475,7 @@ __global__ __launch_bounds__(U_THREADS, 1) void k_tc_update(TcUpdateArgs a) {
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 12) {
+  if (warp == U_MMA_WARP) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
   }

@@ -117,4 +117,40 @@ __device__ __forceinline__ void split4_bf16(float a, float b, float c, float d, 
   lo = make_uint2(pk(l[0], l[1]), pk(l[2], l[3]));
 }
 
+// Exact three-way split: hi is x rounded to 8 significand bits (to nearest, ties to even, on
+// the bit pattern), mid the remainder x - hi rounded the same way, and lo = x - hi - mid,
+// which has at most 8 significant bits and so is a bf16 value as it stands: x = hi + mid + lo
+// exactly for normal FP32 x, with |mid| <= 2^-8 |x| and |lo| <= 2^-16 |x|.  The slices are
+// those of three successive bf16 roundings; integer adds, masks, two subtractions and byte
+// permutes only.  The slices of -x are the negated slices of x.
+__device__ __forceinline__ uint32_t round_bf16_bits(uint32_t b) {
+  return (b + 0x7fffu + ((b >> 16) & 1u)) & 0xffff0000u;
+}
+__device__ __forceinline__ void split_exact(float x, uint32_t& h, uint32_t& m, uint32_t& l) {
+  h = round_bf16_bits(__float_as_uint(x));
+  const float r = x - __uint_as_float(h);
+  m = round_bf16_bits(__float_as_uint(r));
+  l = __float_as_uint(r - __uint_as_float(m));
+}
+// Four values -> three slices, each packed as bf16 pairs in memory order.
+__device__ __forceinline__ void split4_exact(float a, float b, float c, float d, uint2& hi, uint2& mid, uint2& lo) {
+  uint32_t ha, ma, la, hb, mb, lb, hc, mc, lc, hd, md, ld;
+  split_exact(a, ha, ma, la);
+  split_exact(b, hb, mb, lb);
+  split_exact(c, hc, mc, lc);
+  split_exact(d, hd, md, ld);
+  hi = make_uint2(__byte_perm(ha, hb, 0x7632), __byte_perm(hc, hd, 0x7632));
+  mid = make_uint2(__byte_perm(ma, mb, 0x7632), __byte_perm(mc, md, 0x7632));
+  lo = make_uint2(__byte_perm(la, lb, 0x7632), __byte_perm(lc, ld, 0x7632));
+}
+// Two values -> three packed slice words.
+__device__ __forceinline__ void split2_exact(float a, float b, uint32_t& hi, uint32_t& mid, uint32_t& lo) {
+  uint32_t ha, ma, la, hb, mb, lb;
+  split_exact(a, ha, ma, la);
+  split_exact(b, hb, mb, lb);
+  hi = __byte_perm(ha, hb, 0x7632);
+  mid = __byte_perm(ma, mb, 0x7632);
+  lo = __byte_perm(la, lb, 0x7632);
+}
+
 }  // namespace tcx
