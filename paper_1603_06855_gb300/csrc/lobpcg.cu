@@ -292,6 +292,13 @@ __device__ void tri_inv_lower(typename cplx_t<R>::type* L, int n, int ld, typena
   __syncthreads();
 }
 
+// Rotation of one Jacobi plane: s complex, c real, p | q << 16 packed (16 bytes in FP32).
+template <typename R> struct __align__(16) JPlane {
+  typename cplx_t<R>::type s;
+  R c;
+  int pq;
+};
+
 // Two-sided cyclic Jacobi on Hermitian A (n x n, stride ld), accumulating V <- V J.  Pairs
 // are scheduled by the circle method so each round rotates n/2 disjoint planes in parallel.
 // A pair is rotated when |a_pq| > eps sqrt(|a_pp a_qq|) + eps max_{i < nx} |a_ii|, where the
@@ -301,12 +308,14 @@ __device__ void tri_inv_lower(typename cplx_t<R>::type* L, int n, int ld, typena
 //
 // One round is one pass over A: the planes partition the index set, so A splits into 2 x 2
 // blocks (plane t1 rows, plane t2 columns), and J^H A J maps each block to L_t1 M R_t2 on its
-// own.  Only blocks with t1 <= t2 are computed; each writes its conjugate transpose to block
-// (t2, t1), which keeps A exactly Hermitian.  The same pass rotates the column pairs of V.
-// red: 2 blockDim entries.
+// own.  Only blocks with t1 <= t2 are computed (their list is built once); each writes its
+// conjugate transpose to block (t2, t1), which keeps A exactly Hermitian.  The same pass
+// rotates the column pairs of V in chunks of JV_ROWS rows.
+// Scratch: pl (npairs planes), blk (npairs (npairs + 1) / 2 ints), red (2 blockDim).
+#define JV_ROWS 8
 template <typename R>
 __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V, int n, int ld, int nx, int max_sweeps,
-                       R* rc, typename cplx_t<R>::type* rs, int* rp, int* rq, R* red, const int* drop) {
+                       JPlane<R>* pl, int* blk, R* red, const int* drop) {
   typedef typename cplx_t<R>::type C2;
   __shared__ int rotated;
   const int npad = n + (n & 1);
@@ -324,6 +333,12 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
       A[i * ld + i].y = 0;
     }
   }
+  // upper block list (t1 <= t2), packed t1 | t2 << 8
+  const int nA = npairs * (npairs + 1) / 2;
+  for (int e = threadIdx.x; e < npairs * npairs; e += blockDim.x) {
+    const int t1 = e / npairs, t2 = e % npairs;
+    if (t1 <= t2) blk[t1 * npairs - t1 * (t1 - 1) / 2 + (t2 - t1)] = t1 | (t2 << 8);
+  }
   R amax = 0;
   for (int i = threadIdx.x; i < nx; i += blockDim.x)
     if (!drop[i]) amax = fmax(amax, fabs(A[i * ld + i].x));
@@ -335,8 +350,8 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
   }
   const R floor_abs = eps * red[0];
   __syncthreads();
-  const int nA = npairs * npairs;
-  const int nV = npairs * n;
+  const int nch = (n + JV_ROWS - 1) / JV_ROWS;
+  const int nV = npairs * nch;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
@@ -360,19 +375,24 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
             rotated = 1;
           }
         }
-        rp[t] = p; rq[t] = q; rc[t] = c; rs[t] = sp;
+        JPlane<R> w;
+        w.c = c;
+        w.s = sp;
+        w.pq = p | (q << 16);
+        pl[t] = w;
       }
       __syncthreads();
       for (int e = threadIdx.x; e < nA + nV; e += blockDim.x) {
         if (e < nA) {
           // block (t1, t2) of A: rows p1, q1 and columns p2, q2
-          const int t1 = e / npairs, t2 = e % npairs;
-          if (t1 > t2) continue;
-          const C2 s1 = rs[t1], s2 = rs[t2];
+          const int tt12 = blk[e];
+          const int t1 = tt12 & 255, t2 = tt12 >> 8;
+          const JPlane<R> w1 = pl[t1], w2 = pl[t2];
+          const C2 s1 = w1.s, s2 = w2.s;
           const bool a1 = (s1.x != 0 || s1.y != 0), a2 = (s2.x != 0 || s2.y != 0);
           if (!a1 && !a2) continue;
-          const R c1 = rc[t1], c2 = rc[t2];
-          const int p1 = rp[t1], q1 = rq[t1], p2 = rp[t2], q2 = rq[t2];
+          const R c1 = w1.c, c2 = w2.c;
+          const int p1 = w1.pq & 0xffff, q1 = w1.pq >> 16, p2 = w2.pq & 0xffff, q2 = w2.pq >> 16;
           const bool v1 = q1 < n, v2 = q2 < n;
           const C2 z = mk<R>(0, 0);
           C2 m00 = A[p1 * ld + p2];
@@ -404,16 +424,22 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
             if (v1 && v2) { A[q1 * ld + q2] = m11; A[q2 * ld + q1] = cconj(m11); }
           }
         } else {
-          // row i of V, column pair t: V <- V J (consecutive threads walk rows)
+          // rows i0 .. i0 + JV_ROWS of V, column pair of plane t: V <- V J
           const int e2 = e - nA;
-          const int t = e2 / n, i = e2 % n;
-          const C2 sp = rs[t];
+          const int t = e2 / nch, i0 = (e2 - t * nch) * JV_ROWS;
+          const JPlane<R> w = pl[t];
+          const C2 sp = w.s;
           if (sp.x == 0 && sp.y == 0) continue;
-          const int p = rp[t], q = rq[t];
-          const R c = rc[t];
-          const C2 vip = V[i * ld + p], viq = V[i * ld + q];
-          V[i * ld + p] = csub(cscale(vip, c), cmul(cconj(sp), viq));
-          V[i * ld + q] = cadd(cmul(sp, vip), cscale(viq, c));
+          const int p = w.pq & 0xffff, q = w.pq >> 16;
+          const R c = w.c;
+          const C2 spc = cconj(sp);
+          const int i1 = min(n, i0 + JV_ROWS);
+#pragma unroll 4
+          for (int i = i0; i < i1; ++i) {
+            const C2 vip = V[i * ld + p], viq = V[i * ld + q];
+            V[i * ld + p] = csub(cscale(vip, c), cmul(spc, viq));
+            V[i * ld + q] = cadd(cmul(sp, vip), cscale(viq, c));
+          }
         }
       }
       __syncthreads();
@@ -425,14 +451,14 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
   __syncthreads();
 }
 
-#define SMALL_THREADS 512
+#define SMALL_THREADS 1024
 template <typename R> struct SmallSmem {
   static int ld(int n) { return n + ((n & 1) ? 0 : 1); }
   static size_t bytes(int n) {
     typedef typename cplx_t<R>::type C2;
     const int L = ld(n);
-    return sizeof(C2) * (2 * (size_t)n * L + n + 64) + sizeof(R) * (3 * n + 64 + 2 * SMALL_THREADS) +
-           sizeof(int) * (3 * n + 128);
+    return sizeof(C2) * (2 * (size_t)n * L + n) + sizeof(JPlane<R>) * 64 + sizeof(R) * (2 * n + 2 * SMALL_THREADS) +
+           sizeof(int) * (2 * n + 64 * 65 / 2 + 16);
   }
 };
 
@@ -447,19 +473,15 @@ __global__ __launch_bounds__(SMALL_THREADS) void k_small_rr(const typename cplx_
   const int ld = n + ((n & 1) ? 0 : 1);
   C2* A = (C2*)smem;                 // n*ld
   C2* B = A + n * ld;                // n*ld
-  C2* tmp = B + n * ld;              // n
-  C2* rs = tmp + n;                  // 64
-  R* D = (R*)(rs + 64);              // n
+  JPlane<R>* pl = (JPlane<R>*)(B + n * ld);  // 64 planes
+  C2* tmp = (C2*)(pl + 64);          // n
+  R* D = (R*)(tmp + n);              // n
   R* ev = D + n;                     // n
-  R* rc = ev + n;                    // 64
-  R* red = rc + 64;                  // 2 * SMALL_THREADS
-  R* spare = red + 2 * SMALL_THREADS;  // n
-  int* drop = (int*)(spare + n);     // n
+  R* red = ev + n;                   // 2 * SMALL_THREADS
+  int* drop = (int*)(red + 2 * SMALL_THREADS);  // n
   int* perm = drop + n;              // n
-  int* rp = perm + n;                // 64
-  int* rq = rp + 64;                 // 64
-  int* cnt = rq + 64;
-  (void)spare;
+  int* blk = perm + n;               // 64 * 65 / 2 upper blocks
+  int* cnt = blk + 64 * 65 / 2;
   const int k = blockIdx.x;
   const C2* ga = GA + (long long)k * n * n;
   const C2* go = GO + (long long)k * n * n;
@@ -538,7 +560,7 @@ __global__ __launch_bounds__(SMALL_THREADS) void k_small_rr(const typename cplx_
     }
   }
   __syncthreads();
-  jacobi<R>(A, B, n, ld, m, 30, rc, rs, rp, rq, red, drop);
+  jacobi<R>(A, B, n, ld, m, 30, pl, blk, red, drop);
   for (int i = threadIdx.x; i < n; i += blockDim.x) ev[i] = A[i * ld + i].x;
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
