@@ -213,13 +213,33 @@ __global__ void k_resnorm(const typename cplx_t<R>::type* __restrict__ AX, const
 }
 // Number of k-points with a wanted band above tolerance.  A k-point whose wanted bands
 // are all below tolerance is locked for good (kdone = 1): its block is no longer updated.
-__global__ void k_count_unconv(const int* __restrict__ active, int nk, int m, int nb, int* __restrict__ kdone, int* out) {
+// Stagnation: the carried FP32 products A X and Omega X drift by rounding, so a k-point's
+// residual can settle at an attainable floor a little above the tolerance.  A k-point whose
+// worst wanted residual has not dropped below 0.95 of its best for STALL_ITERS iterations and
+// lies within STALL_FACTOR times the tolerance is accepted at that floor.
+#define STALL_ITERS 20
+#define STALL_FACTOR 10.0
+__global__ void k_count_unconv(const int* __restrict__ active, const double* __restrict__ rnorm, double tol, int nk,
+                               int m, int nb, int* __restrict__ kdone, double* __restrict__ best,
+                               int* __restrict__ since, int* out) {
   __shared__ int red[256];
   int c = 0;
   for (int k = threadIdx.x; k < nk; k += blockDim.x) {
     int a = 0;
-    for (int j = 0; j < nb; ++j) a |= active[k * m + j];
+    double worst = 0.0;
+    for (int j = 0; j < nb; ++j) {
+      a |= active[k * m + j];
+      worst = fmax(worst, rnorm[k * m + j]);
+    }
     if (!a) kdone[k] = 1;
+    if (best && !kdone[k]) {
+      if (best[k] == 0.0 || worst < 0.95 * best[k]) {
+        best[k] = worst;
+        since[k] = 0;
+      } else if (++since[k] >= STALL_ITERS && worst <= STALL_FACTOR * tol) {
+        kdone[k] = 1;
+      }
+    }
     c += kdone[k] ? 0 : 1;
   }
   red[threadIdx.x] = c;
@@ -233,15 +253,15 @@ __global__ void k_count_unconv(const int* __restrict__ active, int nk, int m, in
 template <typename R>
 int launch_resnorm(const typename cplx_t<R>::type* AX, const typename cplx_t<R>::type* OX, const R* lam,
                    int nk, int m, int nb, int n3, double tol, double* rnorm, int* active, int* kdone, int* unconv,
-                   cudaStream_t s) {
+                   cudaStream_t s, double* best, int* since) {
   k_resnorm<R><<<nk * m, 256, 0, s>>>(AX, OX, lam, m, nb, n3, tol, rnorm, active);
   PC_LAUNCH_CHECK();
-  k_count_unconv<<<1, 256, 0, s>>>(active, nk, m, nb, kdone, unconv);
+  k_count_unconv<<<1, 256, 0, s>>>(active, rnorm, tol, nk, m, nb, kdone, best, since, unconv);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
-template int launch_resnorm<double>(const double2*, const double2*, const double*, int, int, int, int, double, double*, int*, int*, int*, cudaStream_t);
-template int launch_resnorm<float>(const float2*, const float2*, const float*, int, int, int, int, double, double*, int*, int*, int*, cudaStream_t);
+template int launch_resnorm<double>(const double2*, const double2*, const double*, int, int, int, int, double, double*, int*, int*, int*, cudaStream_t, double*, int*);
+template int launch_resnorm<float>(const float2*, const float2*, const float*, int, int, int, int, double, double*, int*, int*, int*, cudaStream_t, double*, int*);
 
 // Preconditioned residual W = P_q (A x - lambda Omega x) with P_q the inverse of a shifted
 // homogeneous Christoffel operator a I + b K K^T of a reference medium (mean chi):

@@ -63,7 +63,8 @@ struct PrecRef {  // reference medium from the mean of chi (device scalar)
 template <typename R>
 int launch_resnorm(const typename cplx_t<R>::type* AX, const typename cplx_t<R>::type* OX,
                    const R* lam, int nk, int m, int nb, int n3, double tol, double* rnorm,
-                   int* active, int* kdone, int* unconv, cudaStream_t s);
+                   int* active, int* kdone, int* unconv, cudaStream_t s, double* best = nullptr,
+                   int* since = nullptr);
 template <typename R>
 int launch_precond(const typename cplx_t<R>::type* AX, const typename cplx_t<R>::type* OX,
                    const R* lam, const int* active, const int* kdone, int nk, int m, int nb, Geom g,

@@ -265,9 +265,12 @@ __device__ void chol_drop(typename cplx_t<R>::type* B, int n, int ld, R tol, int
 }
 
 // In-place inverse of the lower-triangular L (n x n, stride ld); upper triangle zeroed.
+// Column j of the inverse from columns j+1.. (already inverted): one warp per row, lanes
+// split the dot product and reduce with shuffles.
 template <typename R>
 __device__ void tri_inv_lower(typename cplx_t<R>::type* L, int n, int ld, typename cplx_t<R>::type* tmp) {
   typedef typename cplx_t<R>::type C2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int j = n - 1; j >= 0; --j) {
     __syncthreads();
     C2 ljj = L[j * ld + j];
@@ -276,11 +279,18 @@ __device__ void tri_inv_lower(typename cplx_t<R>::type* L, int n, int ld, typena
     for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) tmp[i] = L[i * ld + j];
     __syncthreads();
     // new L[i][j] = -ajj * sum_{c=j+1..i} Linv[i][c] * old L[c][j]
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = j + 1 + warp; i < n; i += nw) {
       C2 s = mk<R>(0, 0);
-      for (int c = j + 1; c <= i; ++c) cfma(s, L[i * ld + c], tmp[c]);
-      C2 v = cmul(s, ajj);
-      L[i * ld + j] = mk<R>(-v.x, -v.y);
+      for (int c = j + 1 + lane; c <= i; c += 32) cfma(s, L[i * ld + c], tmp[c]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      if (lane == 0) {
+        C2 v = cmul(s, ajj);
+        L[i * ld + j] = mk<R>(-v.x, -v.y);
+      }
     }
     if (threadIdx.x == 0) L[j * ld + j] = ajj;
   }
@@ -310,7 +320,7 @@ template <typename R> struct __align__(16) JPlane {
 // blocks (plane t1 rows, plane t2 columns), and J^H A J maps each block to L_t1 M R_t2 on its
 // own.  Only blocks with t1 <= t2 are computed (their list is built once); each writes its
 // conjugate transpose to block (t2, t1), which keeps A exactly Hermitian.  The same pass
-// rotates the column pairs of V in chunks of JV_ROWS rows.
+// rotates the column pairs of V, JV_ROWS rows per thread.
 // Scratch: pl (npairs planes), blk (npairs (npairs + 1) / 2 ints), red (2 blockDim).
 #define JV_ROWS 8
 template <typename R>
@@ -424,18 +434,18 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
             if (v1 && v2) { A[q1 * ld + q2] = m11; A[q2 * ld + q1] = cconj(m11); }
           }
         } else {
-          // rows i0 .. i0 + JV_ROWS of V, column pair of plane t: V <- V J
+          // rows c0, c0 + nch, c0 + 2 nch, ... of V, column pair of plane t: V <- V J
+          // (neighbouring lanes take neighbouring rows: distinct banks with the odd stride)
           const int e2 = e - nA;
-          const int t = e2 / nch, i0 = (e2 - t * nch) * JV_ROWS;
+          const int t = e2 / nch, c0 = e2 - t * nch;
           const JPlane<R> w = pl[t];
           const C2 sp = w.s;
           if (sp.x == 0 && sp.y == 0) continue;
           const int p = w.pq & 0xffff, q = w.pq >> 16;
           const R c = w.c;
           const C2 spc = cconj(sp);
-          const int i1 = min(n, i0 + JV_ROWS);
 #pragma unroll 4
-          for (int i = i0; i < i1; ++i) {
+          for (int i = c0; i < n; i += nch) {
             const C2 vip = V[i * ld + p], viq = V[i * ld + q];
             V[i * ld + p] = csub(cscale(vip, c), cmul(spc, viq));
             V[i * ld + q] = cadd(cmul(sp, vip), cscale(viq, c));

@@ -64,6 +64,8 @@ struct pc_ctx {
   void* lam = nullptr;           // nk*m (R)
   double *rnorm = nullptr;
   int *active = nullptr, *d_unconv = nullptr, *kdone = nullptr, *kdone_f = nullptr;
+  double* stall_best = nullptr;  // per k: best worst-wanted residual so far (stagnation test)
+  int* stall_since = nullptr;     // per k: iterations since that best
   // FP64 Rayleigh-Ritz and adjoint
   double2 *Xd = nullptr, *AXd = nullptr, *OXd = nullptr, *Ed = nullptr, *Sd = nullptr, *Th = nullptr, *St = nullptr;
   double2 *gpartd = nullptr, *GAd = nullptr, *GOd = nullptr, *Cd = nullptr;
@@ -206,6 +208,7 @@ static void free_kset(pc_ctx* c) {
   void** vs[] = {&c->gpart, &c->GA, &c->GO, &c->Cc, &c->Ct, &c->lam};
   for (auto v : vs) { if (*v) cudaFree(*v); *v = nullptr; }
   dfree(c->rnorm); dfree(c->active); dfree(c->d_unconv); dfree(c->kdone); dfree(c->kdone_f);
+  dfree(c->stall_best); dfree(c->stall_since);
   dfree(c->Xd); dfree(c->AXd); dfree(c->OXd); dfree(c->Ed); dfree(c->Sd); dfree(c->Th); dfree(c->St);
   dfree(c->gpartd); dfree(c->GAd); dfree(c->GOd); dfree(c->Cd);
   dfree(c->lamd); dfree(c->lam_nd); dfree(c->rnormd); dfree(c->actived);
@@ -364,6 +367,8 @@ extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
   rc |= dalloc(&c->d_unconv, 1);
   rc |= dalloc(&c->kdone, (size_t)nk);
   rc |= dalloc(&c->kdone_f, (size_t)nk);
+  rc |= dalloc(&c->stall_best, (size_t)nk);
+  rc |= dalloc(&c->stall_since, (size_t)nk);
   rc |= dalloc(&c->Xd, nvec * n3);
   rc |= dalloc(&c->AXd, nvec * n3);
   rc |= dalloc(&c->OXd, nvec * n3);
@@ -646,6 +651,8 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
   int rc;
 #define TRY(x) do { rc = (x); if (rc) return rc; } while (0)
   PC_CUDA_TRY(cudaMemsetAsync(c->kdone, 0, sizeof(int) * nk, s));
+  PC_CUDA_TRY(cudaMemsetAsync(c->stall_best, 0, sizeof(double) * nk, s));
+  PC_CUDA_TRY(cudaMemsetAsync(c->stall_since, 0, sizeof(int) * nk, s));
   TRY(launch_init_guess<R>(X, nk, m, c->geom, c->Q, c->seed, s));
   TRY(apply_R<R>(c, X, AX, OX, s));
   {
@@ -672,7 +679,8 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
       ph_end(c, sl, s);
       hasP = false;
     }
-    TRY(launch_resnorm<R>(AX, OX, lam, nk, m, nb, n3, c->prm.tol, c->rnorm, c->active, c->kdone, c->d_unconv, s));
+    TRY(launch_resnorm<R>(AX, OX, lam, nk, m, nb, n3, c->prm.tol, c->rnorm, c->active, c->kdone, c->d_unconv, s,
+                          c->stall_best, c->stall_since));
     PC_CUDA_TRY(cudaMemcpyAsync(c->h_unconv, c->d_unconv, sizeof(int), cudaMemcpyDeviceToHost, s));
     PC_CUDA_TRY(cudaStreamSynchronize(s));
     c->unconv = *c->h_unconv;
@@ -680,12 +688,17 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
       const int nv = nk * m;
       std::vector<double> h(nv);
       cudaMemcpy(h.data(), c->rnorm, sizeof(double) * nv, cudaMemcpyDeviceToHost);
-      double mx = 0;
-      int kmx = 0;
+      std::vector<int> kd(nk);
+      cudaMemcpy(kd.data(), c->kdone, sizeof(int) * nk, cudaMemcpyDeviceToHost);
+      double mx = 0, mxo = 0;
+      int kmx = 0, kmxo = -1;
       for (int k = 0; k < nk; ++k)
-        for (int j = 0; j < nb; ++j)
+        for (int j = 0; j < nb; ++j) {
           if (h[k * m + j] > mx) { mx = h[k * m + j]; kmx = k; }
-      fprintf(stderr, "[pc] it %d unconverged_k %d max_res %.3e at k %d\n", it, c->unconv, mx, kmx);
+          if (!kd[k] && h[k * m + j] > mxo) { mxo = h[k * m + j]; kmxo = k; }
+        }
+      fprintf(stderr, "[pc] it %d unconverged_k %d max_res %.3e at k %d; open k: max_res %.3e at k %d\n", it,
+              c->unconv, mx, kmx, mxo, kmxo);
       const char* dk = getenv("PC_DEBUG_K");
       if (dk) {
         int kk = atoi(dk);
