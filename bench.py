@@ -242,6 +242,7 @@ def main():
         ck = clocks.stop()
         ms = e0.elapsed_time(e1)
         st = s.stats()
+        run.last = ((warmup + steps - 1) % len(rhos), omega)
         return s, ms, st, ck
 
     # ---- mixed form (headline) ----
@@ -324,6 +325,18 @@ def main():
         v64 = w0.nk / (ms64 / args.fp64_steps * 1e-3)
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps, "iterations": st64.iterations,
                 "mixed_over_fp64": value / world / v64}
+        # accuracy of the headline form: mixed and FP64 frequencies of the same design (untimed);
+        # relative to max(w_fp64, 0.05 max w_fp64), Gamma zero modes (w < 1e-4 max w) left out
+        d64, om64 = run.last
+        om_mx = torch.empty_like(om64)
+        s_mx.set_design(rhos[d64])
+        s_mx.bands(out=om_mx)
+        torch.cuda.synchronize(dev)
+        a, b = om_mx.cpu().numpy(), om64.cpu().numpy()
+        err = np.abs(a - b) / np.maximum(b, 0.05 * b.max())
+        err[b < 1e-4 * b.max()] = 0.0
+        fp64["omega_max_rel_err_mixed_vs_fp64"] = float(err.max())
+        fp64["omega_compared"] = f"design {d64}, {b.size} (k, band) pairs"
         s64.close()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -23,8 +23,8 @@ struct SetupArgs {
   double2* sfac;    // 3 x L^3
   double2* T;       // 3 x N x N   (density, f1, f2), SI
   double2* W;       // 2 x N x N   inverses of the f1, f2 blocks, SI
-  double2* gj_row;  // 2 x 2 x N
-  double2* gj_col;  // 2 x 2 x N
+  double2* gj_row;  // 2 x 32 x N: old pivot rows of the blocked Gauss-Jordan step
+  double2* gj_col;  // 2 x 32 x (N + 32): pivot-block inverses and column panels
   int* status;
 };
 int launch_setup(const SetupArgs& a, cudaStream_t s);

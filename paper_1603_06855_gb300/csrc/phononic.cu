@@ -322,8 +322,8 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
   rc |= dalloc(&c->sfac, 3 * L * L * L);
   rc |= dalloc(&c->T, 3 * NN);
   rc |= dalloc(&c->W, 2 * NN);
-  rc |= dalloc(&c->gj_row, 4 * (size_t)N);
-  rc |= dalloc(&c->gj_col, 4 * (size_t)N);
+  rc |= dalloc(&c->gj_row, 2 * 32 * (size_t)N);              // blocked Gauss-Jordan: old pivot rows
+  rc |= dalloc(&c->gj_col, 2 * 32 * ((size_t)N + 32));       // pivot-block inverses, column panels
   rc |= dalloc(&c->status, 1);
   if (p->precision == PC_MIXED) {
     rc |= dalloc(&c->Wf, 2 * NN);

@@ -118,47 +118,98 @@ __global__ void k_toeplitz(const double2* __restrict__ sf, int M, double V, doub
   T[t] = cscale(v, V);
 }
 
-// In-place Gauss-Jordan inversion of Hermitian positive definite matrices (no pivoting
-// is needed for HPD).  Step k turns column k into the inverse's column k.  The pivot
-// row and column are read from a snapshot written by the previous step, so one launch
-// per pivot suffices; blockIdx.z selects the matrix.
-__global__ void k_gj_snapshot(const double2* __restrict__ A, int N, long long mstride,
-                              double2* __restrict__ rowbuf, double2* __restrict__ colbuf) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int z = blockIdx.z;
-  if (i >= N) return;
-  rowbuf[(long long)z * N + i] = A[z * mstride + i];                 // row 0
-  colbuf[(long long)z * N + i] = A[z * mstride + (long long)i * N];  // column 0
-}
-
-__global__ void k_gj_step(double2* __restrict__ A, int N, long long mstride, int k,
-                          const double2* __restrict__ row_in, const double2* __restrict__ col_in,
-                          double2* __restrict__ row_out, double2* __restrict__ col_out) {
-  __shared__ double2 ip_s;
+// In-place blocked Gauss-Jordan inversion of Hermitian positive definite matrices (no
+// pivoting is needed for HPD).  For the pivot block [k0, k0 + bb) with P = A11^-1, one panel
+// step maps
+//   A11 <- P,   A1j <- P A1j,   Ai1 <- -Ai1 P,   Aij <- Aij - Ai1 P A1j   (i, j outside the block),
+// which is bb scalar Gauss-Jordan steps at once.  Three launches per panel: the pivot block
+// inverse (with a copy of the old pivot rows), the column panel Ai1 P, and the update of the
+// whole matrix.  blockIdx.z selects the matrix.
+#define GJ_B 32
+__global__ void k_gj_pivot(const double2* __restrict__ A, int N, long long mstride, int k0, int bb,
+                           double2* __restrict__ Pbuf, double2* __restrict__ Ar) {
+  __shared__ double2 P[GJ_B * (GJ_B + 1)];
+  __shared__ double2 prow[GJ_B], pcol[GJ_B];
   const int z = blockIdx.z;
-  const double2* rk = row_in + (long long)z * N;
-  const double2* ck = col_in + (long long)z * N;
-  if (threadIdx.x == 0) {  // 1 / pivot, once per block (FP64 division is expensive here)
-    double2 piv = rk[k];
-    double den = piv.x * piv.x + piv.y * piv.y;
-    ip_s = make_double2(piv.x / den, -piv.y / den);
+  const double2* Az = A + z * mstride;
+  const int ld = GJ_B + 1;
+  for (int t = threadIdx.x; t < bb * bb; t += blockDim.x) {
+    int r = t / bb, c = t % bb;
+    P[r * ld + c] = Az[(long long)(k0 + r) * N + k0 + c];
+  }
+  // old pivot rows for the update of the rest of the matrix
+  double2* arz = Ar + (long long)z * GJ_B * N;
+  for (long long t = threadIdx.x; t < (long long)bb * N; t += blockDim.x) {
+    int r = (int)(t / N), c = (int)(t % N);
+    arz[(long long)r * N + c] = Az[(long long)(k0 + r) * N + c];
   }
   __syncthreads();
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int i = blockIdx.y;
-  if (j >= N) return;
-  const double2 ip = ip_s;
-  double2* a = A + z * mstride + (long long)i * N + j;
-  double2 v;
-  if (i == k && j == k) v = ip;
-  else if (i == k) v = cmul(rk[j], ip);
-  else if (j == k) v = cmul(make_double2(-ck[i].x, -ck[i].y), ip);
-  else v = csub(*a, cmul(ck[i], cmul(rk[j], ip)));
-  *a = v;
-  if (k + 1 < N) {
-    if (i == k + 1) row_out[(long long)z * N + j] = v;
-    if (j == k + 1) col_out[(long long)z * N + i] = v;
+  for (int k = 0; k < bb; ++k) {
+    if ((int)threadIdx.x < bb) {
+      prow[threadIdx.x] = P[k * ld + threadIdx.x];
+      pcol[threadIdx.x] = P[threadIdx.x * ld + k];
+    }
+    __syncthreads();
+    const double2 piv = prow[k];
+    const double den = piv.x * piv.x + piv.y * piv.y;
+    const double2 ip = make_double2(piv.x / den, -piv.y / den);
+    for (int t = threadIdx.x; t < bb * bb; t += blockDim.x) {
+      int r = t / bb, c = t % bb;
+      double2 v;
+      if (r == k && c == k) v = ip;
+      else if (r == k) v = cmul(prow[c], ip);
+      else if (c == k) v = cmul(make_double2(-pcol[r].x, -pcol[r].y), ip);
+      else v = csub(P[r * ld + c], cmul(pcol[r], cmul(prow[c], ip)));
+      P[r * ld + c] = v;
+    }
+    __syncthreads();
   }
+  double2* pz = Pbuf + (long long)z * GJ_B * GJ_B;
+  for (int t = threadIdx.x; t < bb * bb; t += blockDim.x) pz[t] = P[(t / bb) * ld + t % bb];
+}
+
+// Cp[i][l] = sum_m A[i][k0 + m] P[m][l]: the old column panel times the pivot-block inverse.
+__global__ void k_gj_colpanel(const double2* __restrict__ A, int N, long long mstride, int k0, int bb,
+                              const double2* __restrict__ Pbuf, double2* __restrict__ Cp) {
+  const int z = blockIdx.z;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)N * bb) return;
+  const int i = (int)(t / bb), l = (int)(t % bb);
+  const double2* arow = A + z * mstride + (long long)i * N + k0;
+  const double2* pz = Pbuf + (long long)z * GJ_B * GJ_B;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int m = 0; m < bb; ++m) cfma(acc, arow[m], pz[m * bb + l]);
+  Cp[(long long)z * GJ_B * N + (long long)i * GJ_B + l] = acc;
+}
+
+// Whole-matrix update of one panel step; one row i per blockIdx.y.
+__global__ void k_gj_update(double2* __restrict__ A, int N, long long mstride, int k0, int bb,
+                            const double2* __restrict__ Pbuf, const double2* __restrict__ Ar,
+                            const double2* __restrict__ Cp) {
+  __shared__ double2 crow[GJ_B];
+  const int z = blockIdx.z, i = blockIdx.y;
+  const double2* arz = Ar + (long long)z * GJ_B * N;
+  const double2* pz = Pbuf + (long long)z * GJ_B * GJ_B;
+  const bool iblk = i >= k0 && i < k0 + bb;
+  if ((int)threadIdx.x < bb)
+    crow[threadIdx.x] = iblk ? pz[(i - k0) * bb + threadIdx.x] : Cp[(long long)z * GJ_B * N + (long long)i * GJ_B + threadIdx.x];
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double2* a = A + z * mstride + (long long)i * N + j;
+  const bool jblk = j >= k0 && j < k0 + bb;
+  double2 v;
+  if (iblk && jblk) {
+    v = crow[j - k0];                        // P
+  } else if (jblk) {
+    const double2 c = crow[j - k0];          // -Ai1 P
+    v = make_double2(-c.x, -c.y);
+  } else {
+    double2 acc = make_double2(0.0, 0.0);    // (P or Ai1 P) times the old pivot rows
+    for (int l = 0; l < bb; ++l) cfma(acc, crow[l], arz[(long long)l * N + j]);
+    v = iblk ? acc : csub(*a, acc);
+  }
+  *a = v;
 }
 
 // Copies the f1 and f2 Toeplitz operators into the workspace that is inverted in place.
@@ -191,16 +242,14 @@ int launch_setup(const SetupArgs& a, cudaStream_t s) {
   // W1 = T_f1^-1, W2 = T_f2^-1
   k_copy2<<<cdiv(2 * NN, 256), 256, 0, s>>>(a.T + NN, a.W, 2 * NN);
   PC_LAUNCH_CHECK();
-  dim3 gs(cdiv(N, 256), 1, 2);
-  k_gj_snapshot<<<gs, 256, 0, s>>>(a.W, N, NN, a.gj_row, a.gj_col);
-  PC_LAUNCH_CHECK();
-  for (int k = 0; k < N; ++k) {
-    dim3 g(cdiv(N, 256), N, 2);
-    const double2* rin = a.gj_row + (k & 1) * 2LL * N;
-    const double2* cin = a.gj_col + (k & 1) * 2LL * N;
-    double2* rout = a.gj_row + ((k + 1) & 1) * 2LL * N;
-    double2* cout = a.gj_col + ((k + 1) & 1) * 2LL * N;
-    k_gj_step<<<g, 256, 0, s>>>(a.W, N, NN, k, rin, cin, rout, cout);
+  double2* Pbuf = a.gj_col;                          // 2 x GJ_B x GJ_B
+  double2* Cp = a.gj_col + 2LL * GJ_B * GJ_B;       // 2 x N x GJ_B
+  double2* Ar = a.gj_row;                            // 2 x GJ_B x N
+  for (int k0 = 0; k0 < N; k0 += GJ_B) {
+    const int bb = min(GJ_B, N - k0);
+    k_gj_pivot<<<dim3(1, 1, 2), 512, 0, s>>>(a.W, N, NN, k0, bb, Pbuf, Ar);
+    k_gj_colpanel<<<dim3(cdiv((long long)N * bb, 256), 1, 2), 256, 0, s>>>(a.W, N, NN, k0, bb, Pbuf, Cp);
+    k_gj_update<<<dim3(cdiv(N, 256), N, 2), 256, 0, s>>>(a.W, N, NN, k0, bb, Pbuf, Ar, Cp);
   }
   PC_LAUNCH_CHECK();
   return PC_OK;
