@@ -114,53 +114,54 @@ __global__ __launch_bounds__(G_THREADS, 1) void k_tc_gram(TcGramArgs a) {
     // Every load of a stage is issued before any is used, and the loads of stage it + 1 are
     // in flight while stage it is split and stored: one HBM latency per stage, overlapped.
     const int nitems = (ca + cb) * 16;
+    // Item u of this thread is the same column and row pair in every stage: its source
+    // column and its shared-memory offsets are computed once.
+    const float2* colp[G_MAXI];
+    uint32_t off1[G_MAXI], off2[G_MAXI];
+    int qq[G_MAXI];
+#pragma unroll
+    for (int u = 0; u < G_MAXI; ++u) {
+      const int e = threadIdx.x + u * G_PRODUCERS;
+      const int c = e < nitems ? e >> 4 : 0, q = e & 15;
+      const bool isA = c < ca;
+      const int col = isA ? c : c - ca;
+      const int b = col / a.m;
+      const float2* base_p = isA ? (b == 0 ? a.A[0] : (b == 1 ? a.A[1] : a.A[2]))
+                                 : (b == 0 ? a.B[0] : (b == 1 ? a.B[1] : a.B[2]));
+      colp[u] = base_p + kofs + (long long)(col - b * a.m) * a.n3;
+      qq[u] = e < nitems ? 2 * q : 1 << 30;  // rows of an unused item never pass the bound
+      off1[u] = isA ? sw128_offset(col, 8 * q) : 3 * A_SLICE + sw128_offset(col, 8 * q);
+      off2[u] = isA ? 0xffffffffu : 3 * A_SLICE + sw128_offset(cb + col, 8 * q);
+    }
     float2 va[2][G_MAXI], vb[2][G_MAXI];
     auto fetch = [&](int it, float2 (&x0)[G_MAXI], float2 (&x1)[G_MAXI]) {
       const int r0 = r_begin + it * 32;
 #pragma unroll
       for (int u = 0; u < G_MAXI; ++u) {
-        const int e = threadIdx.x + u * G_PRODUCERS;
-        x0[u] = make_float2(0.f, 0.f);
-        x1[u] = make_float2(0.f, 0.f);
-        if (e < nitems) {
-          const int c = e >> 4, q = e & 15;
-          const bool isA = c < ca;
-          const int col = isA ? c : c - ca;
-          const int b = col / a.m;
-          const float2* base_p = isA ? (b == 0 ? a.A[0] : (b == 1 ? a.A[1] : a.A[2]))
-                                     : (b == 0 ? a.B[0] : (b == 1 ? a.B[1] : a.B[2]));
-          const float2* src = base_p + kofs + (long long)(col - b * a.m) * a.n3;
-          const int r = r0 + 2 * q;
-          if (r < r_end) x0[u] = src[r];
-          if (r + 1 < r_end) x1[u] = src[r + 1];
-        }
+        const int r = r0 + qq[u];
+        x0[u] = r < r_end ? colp[u][r] : make_float2(0.f, 0.f);
+        x1[u] = r + 1 < r_end ? colp[u][r + 1] : make_float2(0.f, 0.f);
       }
     };
     auto stash = [&](int it, const float2 (&x0)[G_MAXI], const float2 (&x1)[G_MAXI]) {
-      const int s = it & 1;
-      unsigned char* stp = gbase + s * G_STAGE;
-      unsigned char* bp = stp + 3 * A_SLICE;
+      unsigned char* stp = gbase + (it & 1) * G_STAGE;
 #pragma unroll
       for (int u = 0; u < G_MAXI; ++u) {
-        const int e = threadIdx.x + u * G_PRODUCERS;
-        if (e < nitems) {
-          const int c = e >> 4, q = e & 15;
+        if (qq[u] < 32) {
           uint2 h, mi, lo;
           split4_exact(x0[u].x, x0[u].y, x1[u].x, x1[u].y, h, mi, lo);
-          if (c < ca) {
-            const uint32_t off = sw128_offset(c, 8 * q);
-            *reinterpret_cast<uint2*>(stp + off) = h;
-            *reinterpret_cast<uint2*>(stp + A_SLICE + off) = mi;
-            *reinterpret_cast<uint2*>(stp + 2 * A_SLICE + off) = lo;
+          const uint32_t o1 = off1[u], o2 = off2[u];
+          if (o2 == 0xffffffffu) {
+            *reinterpret_cast<uint2*>(stp + o1) = h;
+            *reinterpret_cast<uint2*>(stp + A_SLICE + o1) = mi;
+            *reinterpret_cast<uint2*>(stp + 2 * A_SLICE + o1) = lo;
           } else {
-            const int col = c - ca;
-            const uint32_t o1 = sw128_offset(col, 8 * q), o2 = sw128_offset(cb + col, 8 * q);
-            *reinterpret_cast<uint2*>(bp + o1) = h;
-            *reinterpret_cast<uint2*>(bp + G_B_SLICE + o1) = mi;
-            *reinterpret_cast<uint2*>(bp + 2 * G_B_SLICE + o1) = lo;
-            *reinterpret_cast<uint2*>(bp + o2) = make_uint2(rot_pair(h.x), rot_pair(h.y));
-            *reinterpret_cast<uint2*>(bp + G_B_SLICE + o2) = make_uint2(rot_pair(mi.x), rot_pair(mi.y));
-            *reinterpret_cast<uint2*>(bp + 2 * G_B_SLICE + o2) = make_uint2(rot_pair(lo.x), rot_pair(lo.y));
+            *reinterpret_cast<uint2*>(stp + o1) = h;
+            *reinterpret_cast<uint2*>(stp + G_B_SLICE + o1) = mi;
+            *reinterpret_cast<uint2*>(stp + 2 * G_B_SLICE + o1) = lo;
+            *reinterpret_cast<uint2*>(stp + o2) = make_uint2(rot_pair(h.x), rot_pair(h.y));
+            *reinterpret_cast<uint2*>(stp + G_B_SLICE + o2) = make_uint2(rot_pair(mi.x), rot_pair(mi.y));
+            *reinterpret_cast<uint2*>(stp + 2 * G_B_SLICE + o2) = make_uint2(rot_pair(lo.x), rot_pair(lo.y));
           }
         }
       }
@@ -243,7 +244,7 @@ constexpr int U_KMAX = 192;     // padded real K (2 * 72 input columns -> 144 ->
 constexpr int U_NMAX = 96;
 constexpr int U_BOP = 3 * U_NMAX * U_KMAX * 2;  // coefficient operand, three slices
 constexpr int U_STAGE = 3 * A_SLICE;
-constexpr int U_SMEM = U_BOP + 2 * U_STAGE + 256 + 1024;
+constexpr int U_SMEM = U_BOP + 2 * U_STAGE + 256 + 72 * 8 + 1024;  // + input column table
 constexpr int U_MAXI = 128 * 16 / U_PRODUCERS;  // staged items per thread and stage
 
 struct TcUpdateArgs {
@@ -269,6 +270,7 @@ __global__ __launch_bounds__(U_THREADS, 1) void k_tc_update(TcUpdateArgs a) {
   // barriers: full[s] +8s, empty[s] +16+8s, tfull[b] +32+8b, tempty[b] +48+8b, done +64
   const uint32_t bars = stg + 2 * U_STAGE;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + U_BOP + 2 * U_STAGE + 128);
+  const float2** colp = reinterpret_cast<const float2**>(gbase + U_BOP + 2 * U_STAGE + 256);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.x, t = blockIdx.y;
   const int ncols = a.nblk * a.m;           // complex input columns
@@ -339,6 +341,11 @@ __global__ __launch_bounds__(U_THREADS, 1) void k_tc_update(TcUpdateArgs a) {
         *reinterpret_cast<uint32_t*>(gbase + (size_t)(sl * nat + at) * NP * 128 + off) = w[sl];
     }
   }
+  // first element of every input column of this (k, triplet)
+  for (int i = threadIdx.x; i < ncols; i += U_THREADS) {
+    const int b = i / a.m;
+    colp[i] = a.in[t][b] + (long long)k * a.in_kstride + (long long)(i - b * a.m) * a.n3;
+  }
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -348,49 +355,47 @@ __global__ __launch_bounds__(U_THREADS, 1) void k_tc_update(TcUpdateArgs a) {
 
   if (warp < U_EPI_WARP) {
     // All loads of a stage are issued together; the next stage's loads are in flight while
-    // the current one is split and stored.
+    // the current one is split and stored.  A warp covers 8 rows x 4 column pairs, so its
+    // 8-byte stores under the 128-byte swizzle touch every bank exactly twice (no conflicts).
     float2 pa[2][U_MAXI], pb[2][U_MAXI];
+    // item u of this thread: the same row and K column pair in every stage
+    int rr_u[U_MAXI], ip_u[U_MAXI];
+    uint32_t off_u[U_MAXI];
+#pragma unroll
+    for (int u = 0; u < U_MAXI; ++u) {
+      const int e = threadIdx.x + u * U_PRODUCERS;
+      rr_u[u] = 8 * ((e >> 5) & 15) + (e & 7);
+      ip_u[u] = 4 * (e >> 9) + ((e >> 3) & 3);
+      off_u[u] = sw128_offset(rr_u[u], 8 * ip_u[u]);
+    }
     auto fetch = [&](int it, float2 (&x0)[U_MAXI], float2 (&x1)[U_MAXI]) {
       const int tl = it / nat, at = it % nat;
       const int r0 = (tile0 + tl) * 128;
       const int nip = min(64, ((Kt - 64 * at + 15) / 16) * 16) / 4;
-      const float2* const* inp = a.in[t];
 #pragma unroll
       for (int u = 0; u < U_MAXI; ++u) {
-        const int e = threadIdx.x + u * U_PRODUCERS;
         x0[u] = make_float2(0.f, 0.f);
         x1[u] = make_float2(0.f, 0.f);
-        const int rr = e & 127, ip = e >> 7;
-        const int r = r0 + rr;
-        const int i0 = 32 * at + 2 * ip;
-        if (ip < nip && r < a.n3) {
-          if (i0 < ncols) {
-            const int b = i0 / a.m;
-            x0[u] = inp[b][(long long)k * a.in_kstride + (long long)(i0 - b * a.m) * a.n3 + r];
-          }
-          if (i0 + 1 < ncols) {
-            const int b = (i0 + 1) / a.m;
-            x1[u] = inp[b][(long long)k * a.in_kstride + (long long)(i0 + 1 - b * a.m) * a.n3 + r];
-          }
+        const int r = r0 + rr_u[u];
+        const int i0 = 32 * at + 2 * ip_u[u];
+        if (ip_u[u] < nip && r < a.n3) {
+          if (i0 < ncols) x0[u] = colp[i0][r];
+          if (i0 + 1 < ncols) x1[u] = colp[i0 + 1][r];
         }
       }
     };
     auto stash = [&](int it, const float2 (&x0)[U_MAXI], const float2 (&x1)[U_MAXI]) {
-      const int s = it & 1;
       const int at = it % nat;
       const int nip = min(64, ((Kt - 64 * at + 15) / 16) * 16) / 4;
-      unsigned char* stp = gbase + U_BOP + s * U_STAGE;
+      unsigned char* stp = gbase + U_BOP + (it & 1) * U_STAGE;
 #pragma unroll
       for (int u = 0; u < U_MAXI; ++u) {
-        const int e = threadIdx.x + u * U_PRODUCERS;
-        const int rr = e & 127, ip = e >> 7;
-        if (ip < nip) {
+        if (ip_u[u] < nip) {
           uint2 h, mi, lo;
           split4_exact(x0[u].x, x0[u].y, x1[u].x, x1[u].y, h, mi, lo);
-          const uint32_t off = sw128_offset(rr, 8 * ip);
-          *reinterpret_cast<uint2*>(stp + off) = h;
-          *reinterpret_cast<uint2*>(stp + A_SLICE + off) = mi;
-          *reinterpret_cast<uint2*>(stp + 2 * A_SLICE + off) = lo;
+          *reinterpret_cast<uint2*>(stp + off_u[u]) = h;
+          *reinterpret_cast<uint2*>(stp + A_SLICE + off_u[u]) = mi;
+          *reinterpret_cast<uint2*>(stp + 2 * A_SLICE + off_u[u]) = lo;
         }
       }
     };
