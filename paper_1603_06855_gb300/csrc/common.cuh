@@ -1,6 +1,7 @@
 // Shared device helpers: complex arithmetic templated on the real type, launch
 // checks, device status codes.
 #pragma once
+#include <atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "../../include/phononic.h"
@@ -71,7 +72,7 @@ __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(st
   } while (0)
 
 // Every kernel launch is followed by this check, which also counts the launch.
-extern long long g_pc_launches;
+extern std::atomic<long long> g_pc_launches;  // kernel launches (two host threads may launch)
 #define PC_LAUNCH_CHECK()        \
   do {                           \
     ++g_pc_launches;             \

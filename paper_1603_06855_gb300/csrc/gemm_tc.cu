@@ -261,6 +261,7 @@ struct TcPlan {
   CUtensorMap mA_hi[3], mA_mid[3], mA_lo[3], mE[3], mX[3];
   int* status;
   bool ok;
+  bool owns_ops;          // false: the operator slices belong to another plan
 };
 
 TcPlan* tc_plan_create(int N, int nvec, int* status) {
@@ -271,6 +272,7 @@ TcPlan* tc_plan_create(int N, int nvec, int* status) {
   p->Kp = ((2 * N + TC_BK - 1) / TC_BK) * TC_BK;
   p->status = status;
   p->ok = false;
+  p->owns_ops = true;
   size_t asz = (size_t)p->Mp * p->Kp;
   bool good = true;
   for (int i = 0; i < 3; ++i) {
@@ -307,7 +309,7 @@ TcPlan* tc_plan_create(int N, int nvec, int* status) {
 
 void tc_plan_destroy(TcPlan* p) {
   if (!p) return;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 3 && p->owns_ops; ++i) {
     if (p->Ahi[i]) cudaFree(p->Ahi[i]);
     if (p->Amid[i]) cudaFree(p->Amid[i]);
     if (p->Alo[i]) cudaFree(p->Alo[i]);
@@ -319,6 +321,42 @@ void tc_plan_destroy(TcPlan* p) {
 }
 
 bool tc_available(const TcPlan* p) { return p && p->ok; }
+
+TcPlan* tc_plan_create_sharing(const TcPlan* ops, int nvec, int* status) {
+  if (!ops || !ops->ok) return nullptr;
+  TcPlan* p = new TcPlan();
+  p->N = ops->N;
+  p->nvec_max = nvec;
+  p->Mp = ops->Mp;
+  p->Kp = ops->Kp;
+  p->status = status;
+  p->ok = false;
+  p->owns_ops = false;
+  for (int i = 0; i < 3; ++i) {
+    p->Ahi[i] = ops->Ahi[i];
+    p->Amid[i] = ops->Amid[i];
+    p->Alo[i] = ops->Alo[i];
+    p->mA_hi[i] = ops->mA_hi[i];
+    p->mA_mid[i] = ops->mA_mid[i];
+    p->mA_lo[i] = ops->mA_lo[i];
+  }
+  size_t esz = (size_t)6 * nvec * p->Kp, xsz = (size_t)3 * nvec * p->Kp;
+  bool good = cudaMalloc(&p->E, 3 * esz * 2) == cudaSuccess;
+  good &= cudaMalloc(&p->X, 3 * xsz * 2) == cudaSuccess;
+  good &= cudaMalloc(&p->S, (size_t)6 * nvec * p->N * sizeof(float2)) == cudaSuccess;
+  if (!good) {
+    cudaGetLastError();
+    tc_plan_destroy(p);
+    return nullptr;
+  }
+  good = true;
+  for (int t = 0; t < 3; ++t) {
+    good &= make_map(&p->mE[t], p->E + t * esz, (long long)6 * nvec, p->Kp, TC_BN);
+    good &= make_map(&p->mX[t], p->X + t * xsz, (long long)3 * nvec, p->Kp, TC_BN);
+  }
+  p->ok = good;
+  return p;
+}
 
 int tc_prepare_operators(TcPlan* p, const double2* W, const double2* T, double w_scale, double t_scale, cudaStream_t s) {
   if (!p) return PC_OK;

@@ -5,6 +5,9 @@
 struct TcPlan;
 // status: device word that receives PC_ETIMEOUT if a bounded wait expires.
 TcPlan* tc_plan_create(int N, int nvec, int* status);
+// A plan with its own vector workspaces (capacity nvec) that applies the operators prepared in
+// `ops` (which must outlive it); for k-point subsets run concurrently on separate streams.
+TcPlan* tc_plan_create_sharing(const TcPlan* ops, int nvec, int* status);
 void tc_plan_destroy(TcPlan* p);
 bool tc_available(const TcPlan* p);
 // Converts the FP64 operators (W1, W2 in SI; T_rho in SI) into the scaled split-BF16

@@ -15,17 +15,23 @@
 #include <cstring>
 #include <new>
 #include <utility>
+#include <atomic>
+#include <mutex>
+#include <thread>
 #include <vector>
 #include "kernels.h"
 #include "gemm_tc.h"
 
 extern int g_acc64;     // lobpcg.cu: FP64 accumulation switch (experiments)
 
-long long g_pc_launches = 0;
+std::atomic<long long> g_pc_launches{0};
 
 // Per-phase device timing (pc_set_profiling): event pairs recorded on the caller's stream.
 enum { PH_RR_GEMM = 0, PH_ITER_APPLY = 1, PH_SMALL = 2, PH_GRAD = 3, PH_GRAM = 4, PH_UPDATE = 5, PH_LOOP = 6,
        PH_FINAL = 7, PH_COUNT = 8 };
+// Smallest k half worth its own stream (mixed form, see pc_bands).
+constexpr int kSplitMinK = 16;
+
 struct EventPair {
   cudaEvent_t a, b;
   int phase;
@@ -75,6 +81,11 @@ struct pc_ctx {
   int *pairs = nullptr, *npairs = nullptr;
   double2* adj_t2 = nullptr;
   TcPlan* tc = nullptr;
+  TcPlan* tc2 = nullptr;        // workspaces of the second k half (operators shared with tc)
+  cudaStream_t sk[2] = {nullptr, nullptr};  // non-blocking streams of the two k halves
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+  int split = 1;                // PC_SPLIT=0: the block iteration of the mixed form on one stream
+  std::mutex ph_mu;             // profiling records from the two k-half threads
   bool tc_ready = false;        // tensor-core operands prepared for the current design
   int debug = 0;  // PC_DEBUG=1 prints the residual history of the block iteration to stderr
   int profiling = 0;
@@ -96,6 +107,7 @@ struct pc_ctx {
 // Opens a timed phase on stream s (no-op unless profiling); returns the slot index or -1.
 static int ph_begin(pc_ctx* c, int phase, double flops, cudaStream_t s, double bytes = 0.0) {
   if (!c->profiling) return -1;
+  std::lock_guard<std::mutex> lk(c->ph_mu);
   EventPair e;
   if (!c->ev_free.empty()) {
     e = c->ev_free.back();
@@ -112,6 +124,7 @@ static int ph_begin(pc_ctx* c, int phase, double flops, cudaStream_t s, double b
 }
 static void ph_end(pc_ctx* c, int slot, cudaStream_t s) {
   if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(c->ph_mu);
   cudaEventRecord(c->ev_used[slot].b, s);
 }
 // Folds finished event pairs into the sums (caller has synchronised).
@@ -214,6 +227,7 @@ static void free_kset(pc_ctx* c) {
   dfree(c->lamd); dfree(c->lam_nd); dfree(c->rnormd); dfree(c->actived);
   dfree(c->weights); dfree(c->pairs); dfree(c->npairs); dfree(c->adj_t2);
   dfree(c->sGA); dfree(c->sGO); dfree(c->sC); dfree(c->sCP); dfree(c->slam);
+  if (c->tc2) { tc_plan_destroy(c->tc2); c->tc2 = nullptr; }
   if (c->tc) { tc_plan_destroy(c->tc); c->tc = nullptr; }
   c->nk = 0;
   c->have_bands = false;
@@ -233,6 +247,11 @@ extern "C" void pc_destroy(pc_ctx* c) {
   for (auto& e : c->ev_used) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto& e : c->ev_free) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   if (c->h_unconv) cudaFreeHost(c->h_unconv);
+  for (int i = 0; i < 2; ++i) {
+    if (c->sk[i]) cudaStreamDestroy(c->sk[i]);
+    if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;
 }
 
@@ -273,6 +292,8 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
     c->small32 = (s32 && s32[0] == '0') ? 0 : 1;
     const char* sd = getenv("PC_INIT_SEED");
     c->seed = sd ? strtoull(sd, nullptr, 10) : 0ull;
+    const char* sp = getenv("PC_SPLIT");
+    c->split = (sp && sp[0] == '0') ? 0 : 1;
     const char* tt = getenv("PC_TC_TALL");
     g_tc_tall = (tt && tt[0] == '0') ? 0 : 1;
   }
@@ -283,7 +304,13 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
   c->L = 4 * p->M + 1;
   c->ne = p->n[0] * p->n[1] * p->n[2];
   c->nb = p->nbands;
-  c->m = std::min(std::min(p->nbands + 4, 24), N);
+  {
+    // guard vectors beyond the wanted bands: 3 in the mixed form (smaller projected problems,
+    // the same iteration count there), 4 in the FP64 form (fewer iterations); PC_GUARD overrides
+    const char* gv = getenv("PC_GUARD");
+    const int guard = (gv && atoi(gv) >= 1 && atoi(gv) <= 8) ? atoi(gv) : (p->precision == PC_MIXED ? 3 : 4);
+    c->m = std::min(std::min(p->nbands + guard, 24), N);
+  }
   lattice_vectors(p->lattice, p->a, c->A);
   reciprocal(c->A, c->Tm);
   c->V = std::fabs(det3(c->A));
@@ -334,7 +361,12 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
       cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
       cudaEventCreate(&c->ev_s0) != cudaSuccess || cudaEventCreate(&c->ev_s1) != cudaSuccess ||
       cudaEventCreate(&c->ev_g0) != cudaSuccess || cudaEventCreate(&c->ev_g1) != cudaSuccess ||
-      cudaMallocHost((void**)&c->h_unconv, sizeof(int)) != cudaSuccess) {
+      cudaMallocHost((void**)&c->h_unconv, 2 * sizeof(int)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->sk[0], cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->sk[1], cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join[1], cudaEventDisableTiming) != cudaSuccess) {
     pc_destroy(c);
     return PC_ECUDA;
   }
@@ -364,7 +396,7 @@ extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
   if (cudaMalloc(&c->lam, nvec * rsz) != cudaSuccess) { c->lam = nullptr; rc = PC_ENOMEM; }
   rc |= dalloc(&c->rnorm, nvec);
   rc |= dalloc(&c->active, nvec);
-  rc |= dalloc(&c->d_unconv, 1);
+  rc |= dalloc(&c->d_unconv, 2);
   rc |= dalloc(&c->kdone, (size_t)nk);
   rc |= dalloc(&c->kdone_f, (size_t)nk);
   rc |= dalloc(&c->stall_best, (size_t)nk);
@@ -397,6 +429,8 @@ extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
     c->tc = tc_plan_create(N, (int)nvec, c->status);
     c->tc_ready = false;
     if (!c->tc) rc = PC_ENOMEM;
+    // second k half, run concurrently on its own stream (see pc_bands)
+    if (c->tc && nk >= 2 * kSplitMinK) c->tc2 = tc_plan_create_sharing(c->tc, (nk - nk / 2) * m, c->status);
   }
   if (rc != PC_OK) { free_kset(c); return PC_ENOMEM; }
   if (cudaMemcpy(c->Q, q, 3 * sizeof(double) * nk, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -488,7 +522,8 @@ static int apply_fp64(pc_ctx* c, const double2* X, double2* AX, double2* OX, int
 // Nondimensional A' X and Omega' X for FP32 vectors (vector v at k = v / m of Q): the split-BF16
 // tensor-core path when available (PC_TC=0 selects the FP32 CUDA-core GEMM instead).
 static int apply_fp32(pc_ctx* c, const float2* X, float2* AX, float2* OX, int nvec, int m, const double* Q,
-                      cudaStream_t s) {
+                      cudaStream_t s, TcPlan* plan = nullptr) {
+  if (!plan) plan = c->tc;
   if (c->apply64) {  // experiment switch: FP64 operator on widened FP32 vectors
     const long long n = (long long)nvec * 3 * c->N;
     int rc = launch_convert_f2d(X, c->Xd, n, s);
@@ -497,13 +532,13 @@ static int apply_fp32(pc_ctx* c, const float2* X, float2* AX, float2* OX, int nv
     if (!rc) rc = launch_d2f(c->OXd, OX, n, 1.0, s);
     return rc;
   }
-  if (c->use_tc && c->tc && tc_available(c->tc)) {
+  if (c->use_tc && plan && tc_available(plan)) {
     if (!c->tc_ready) {
       int rc = tc_prepare_operators(c->tc, c->W, c->T, c->cA, 1.0 / c->sO, s);
       if (rc) return rc;
       c->tc_ready = true;
     }
-    return tc_apply(c->tc, X, AX, OX, nvec, m, c->geom, Q, s);
+    return tc_apply(plan, X, AX, OX, nvec, m, c->geom, Q, s);
   }
   const int N = c->N;
   const long long NN = (long long)N * N;
@@ -520,19 +555,32 @@ static int apply_fp32(pc_ctx* c, const float2* X, float2* AX, float2* OX, int nv
   return launch_gemm<float>(N, 3 * nvec, N, c->Tf, N, X, N, OX, N, 1.0f, s);
 }
 
+// A subset of the k-points run by one host thread on one stream: k in [k0, k0 + nk).
+struct KSet {
+  int k0 = 0, nk = 0;
+  cudaStream_t s = nullptr;
+  int* d_unconv = nullptr;  // device count of its unconverged k-points
+  int* h_unconv = nullptr;  // pinned host copy
+  int unconv = 0, iterations = 0;
+  TcPlan* tc = nullptr;     // tensor-core workspaces of this subset
+};
+
 template <typename R>
-static int apply_R(pc_ctx* c, const typename Ops<R>::C2* X, typename Ops<R>::C2* AX, typename Ops<R>::C2* OX, cudaStream_t s);
+static int apply_R(pc_ctx* c, const KSet& ks, const typename Ops<R>::C2* X, typename Ops<R>::C2* AX,
+                   typename Ops<R>::C2* OX);
 template <>
-int apply_R<double>(pc_ctx* c, const double2* X, double2* AX, double2* OX, cudaStream_t s) {
-  return apply_fp64(c, X, AX, OX, c->nk * c->m, c->m, c->Q, c->cA, 1.0 / c->sO, (double2*)c->E, (double2*)c->S, s);
+int apply_R<double>(pc_ctx* c, const KSet& ks, const double2* X, double2* AX, double2* OX) {
+  return apply_fp64(c, X, AX, OX, ks.nk * c->m, c->m, c->Q + 3 * ks.k0, c->cA, 1.0 / c->sO, (double2*)c->E,
+                    (double2*)c->S, ks.s);
 }
 template <>
-int apply_R<float>(pc_ctx* c, const float2* X, float2* AX, float2* OX, cudaStream_t s) {
-  return apply_fp32(c, X, AX, OX, c->nk * c->m, c->m, c->Q, s);
+int apply_R<float>(pc_ctx* c, const KSet& ks, const float2* X, float2* AX, float2* OX) {
+  return apply_fp32(c, X, AX, OX, ks.nk * c->m, c->m, c->Q + 3 * ks.k0, ks.s, ks.tc);
 }
 
 template <typename R>
-static UpdateArgs<R> upd(pc_ctx* c, int nblk, int identity_last, const void* Cmat, long long cstride, int cld, int mout) {
+static UpdateArgs<R> upd(pc_ctx* c, int nk, int nblk, int identity_last, const void* Cmat, long long cstride, int cld,
+                         int mout) {
   UpdateArgs<R> u;
   memset(&u, 0, sizeof(u));
   u.nblk = nblk;
@@ -543,7 +591,7 @@ static UpdateArgs<R> upd(pc_ctx* c, int nblk, int identity_last, const void* Cma
   u.m = c->m;
   u.mout = mout;
   u.n3 = 3 * c->N;
-  u.nk = c->nk;
+  u.nk = nk;
   u.in_kstride = (long long)c->m * 3 * c->N;
   u.out_kstride = (long long)mout * 3 * c->N;
   u.ntrip = 3;
@@ -562,47 +610,48 @@ template <> struct SmallTol<double> { static constexpr double pdir_abs = 1e-26; 
 template <> struct SmallTol<float> { static constexpr double pdir_abs = 1e-12; };
 
 template <typename R>
-static int small_rr_any(pc_ctx* c, const typename Ops<R>::C2* GA, const typename Ops<R>::C2* GO, int n, int m,
+static int small_rr_any(pc_ctx* c, int nk, const typename Ops<R>::C2* GA, const typename Ops<R>::C2* GO, int n, int m,
                         const int* kdone, R* lam, typename Ops<R>::C2* cX, typename Ops<R>::C2* cP, cudaStream_t s);
 template <>
-int small_rr_any<double>(pc_ctx* c, const double2* GA, const double2* GO, int n, int m, const int* kdone, double* lam,
-                         double2* cX, double2* cP, cudaStream_t s) {
-  int rc = launch_small_rr<double>(GA, GO, n, m, c->nk, Ops<double>::drop_small, kdone, lam, cX, c->status, s);
-  if (!rc && cP) rc = launch_small_pdir<double>(GO, cX, n, m, c->nk, kdone, SmallTol<double>::pdir_abs, cP, s);
+int small_rr_any<double>(pc_ctx* c, int nk, const double2* GA, const double2* GO, int n, int m, const int* kdone,
+                         double* lam, double2* cX, double2* cP, cudaStream_t s) {
+  int rc = launch_small_rr<double>(GA, GO, n, m, nk, Ops<double>::drop_small, kdone, lam, cX, c->status, s);
+  if (!rc && cP) rc = launch_small_pdir<double>(GO, cX, n, m, nk, kdone, SmallTol<double>::pdir_abs, cP, s);
   return rc;
 }
 template <>
-int small_rr_any<float>(pc_ctx* c, const float2* GA, const float2* GO, int n, int m, const int* kdone, float* lam,
-                        float2* cX, float2* cP, cudaStream_t s) {
+int small_rr_any<float>(pc_ctx* c, int nk, const float2* GA, const float2* GO, int n, int m, const int* kdone,
+                        float* lam, float2* cX, float2* cP, cudaStream_t s) {
   if (c->small32) {
-    int rc = launch_small_rr<float>(GA, GO, n, m, c->nk, Ops<float>::drop_small, kdone, lam, cX, c->status, s);
-    if (!rc && cP) rc = launch_small_pdir<float>(GO, cX, n, m, c->nk, kdone, (float)SmallTol<float>::pdir_abs, cP, s);
+    int rc = launch_small_rr<float>(GA, GO, n, m, nk, Ops<float>::drop_small, kdone, lam, cX, c->status, s);
+    if (!rc && cP) rc = launch_small_pdir<float>(GO, cX, n, m, nk, kdone, (float)SmallTol<float>::pdir_abs, cP, s);
     return rc;
   }
-  const long long nn = (long long)c->nk * n * n;
+  const long long nn = (long long)nk * n * n;
   int rc = launch_convert_f2d(GA, c->sGA, nn, s);
   if (!rc) rc = launch_convert_f2d(GO, c->sGO, nn, s);
-  if (!rc) rc = launch_real_f2d(lam, c->slam, (long long)c->nk * m, s);
-  if (!rc) rc = launch_small_rr<double>(c->sGA, c->sGO, n, m, c->nk, (double)Ops<float>::drop_small, kdone, c->slam,
+  if (!rc) rc = launch_real_f2d(lam, c->slam, (long long)nk * m, s);
+  if (!rc) rc = launch_small_rr<double>(c->sGA, c->sGO, n, m, nk, (double)Ops<float>::drop_small, kdone, c->slam,
                                         c->sC, c->status, s);
-  if (!rc && cP) rc = launch_small_pdir<double>(c->sGO, c->sC, n, m, c->nk, kdone, SmallTol<float>::pdir_abs, c->sCP, s);
-  if (!rc) rc = launch_d2f(c->sC, cX, (long long)c->nk * n * m, 1.0, s);
-  if (!rc && cP) rc = launch_d2f(c->sCP, cP, (long long)c->nk * n * m, 1.0, s);
-  if (!rc) rc = launch_real_d2f(c->slam, lam, (long long)c->nk * m, s);
+  if (!rc && cP) rc = launch_small_pdir<double>(c->sGO, c->sC, n, m, nk, kdone, SmallTol<float>::pdir_abs, c->sCP, s);
+  if (!rc) rc = launch_d2f(c->sC, cX, (long long)nk * n * m, 1.0, s);
+  if (!rc && cP) rc = launch_d2f(c->sCP, cP, (long long)nk * n * m, 1.0, s);
+  if (!rc) rc = launch_real_d2f(c->slam, lam, (long long)nk * m, s);
   return rc;
 }
 template <typename R>
-static int small_chol_any(pc_ctx* c, const typename Ops<R>::C2* G, int m, typename Ops<R>::C2* T, cudaStream_t s);
+static int small_chol_any(pc_ctx* c, int nk, const typename Ops<R>::C2* G, int m, typename Ops<R>::C2* T,
+                          cudaStream_t s);
 template <>
-int small_chol_any<double>(pc_ctx* c, const double2* G, int m, double2* T, cudaStream_t s) {
-  return launch_small_chol<double>(G, m, c->nk, Ops<double>::drop_small, nullptr, 0, 0.0, T, s);
+int small_chol_any<double>(pc_ctx* c, int nk, const double2* G, int m, double2* T, cudaStream_t s) {
+  return launch_small_chol<double>(G, m, nk, Ops<double>::drop_small, nullptr, 0, 0.0, T, s);
 }
 template <>
-int small_chol_any<float>(pc_ctx* c, const float2* G, int m, float2* T, cudaStream_t s) {
-  if (c->small32) return launch_small_chol<float>(G, m, c->nk, Ops<float>::drop_small, nullptr, 0, 0.0f, T, s);
-  int rc = launch_convert_f2d(G, c->sGO, (long long)c->nk * m * m, s);
-  if (!rc) rc = launch_small_chol<double>(c->sGO, m, c->nk, (double)Ops<float>::drop_small, nullptr, 0, 0.0, c->sC, s);
-  if (!rc) rc = launch_d2f(c->sC, T, (long long)c->nk * m * m, 1.0, s);
+int small_chol_any<float>(pc_ctx* c, int nk, const float2* G, int m, float2* T, cudaStream_t s) {
+  if (c->small32) return launch_small_chol<float>(G, m, nk, Ops<float>::drop_small, nullptr, 0, 0.0f, T, s);
+  int rc = launch_convert_f2d(G, c->sGO, (long long)nk * m * m, s);
+  if (!rc) rc = launch_small_chol<double>(c->sGO, m, nk, (double)Ops<float>::drop_small, nullptr, 0, 0.0, c->sC, s);
+  if (!rc) rc = launch_d2f(c->sC, T, (long long)nk * m * m, 1.0, s);
   return rc;
 }
 
@@ -638,29 +687,38 @@ static int update_ph(pc_ctx* c, const UpdateArgs<R>& u, cudaStream_t s) {
 }
 
 template <typename R>
-static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
+static int run_block_iteration(pc_ctx* c, KSet& ks) {
   typedef typename Ops<R>::C2 C2;
-  const int m = c->m, nk = c->nk, n3 = 3 * c->N, nb = c->nb;
+  const int m = c->m, nk = ks.nk, n3 = 3 * c->N, nb = c->nb, k0 = ks.k0;
+  cudaStream_t s = ks.s;
+  // per-k buffers of this subset (the small workspaces at their largest per-k size)
+  const long long G1 = 72LL * 72;
   C2* b[15];
-  for (int i = 0; i < 15; ++i) b[i] = (C2*)c->blk[i];
+  for (int i = 0; i < 15; ++i) b[i] = (C2*)c->blk[i] + (long long)k0 * m * n3;
+  const double* Qk = c->Q + 3 * k0;
+  int* kdone = c->kdone + k0;
+  int* active = c->active + (long long)k0 * m;
+  double* rnorm = c->rnorm + (long long)k0 * m;
+  double* sbest = c->stall_best + k0;
+  int* ssince = c->stall_since + k0;
   C2 *X = b[0], *AX = b[1], *OX = b[2], *Wb = b[3], *AW = b[4], *OW = b[5], *P = b[6], *AP = b[7], *OP = b[8];
   C2 *Xn = b[9], *AXn = b[10], *OXn = b[11], *Pn = b[12], *APn = b[13], *OPn = b[14];
-  C2* part = (C2*)c->gpart;
-  C2 *GA = (C2*)c->GA, *GO = (C2*)c->GO, *Cc = (C2*)c->Cc, *Ct = (C2*)c->Ct;
-  R* lam = (R*)c->lam;
+  C2* part = (C2*)c->gpart + k0 * 8 * G1;
+  C2 *GA = (C2*)c->GA + k0 * G1, *GO = (C2*)c->GO + k0 * G1, *Cc = (C2*)c->Cc + k0 * G1, *Ct = (C2*)c->Ct + k0 * G1;
+  R* lam = (R*)c->lam + (long long)k0 * m;
   int rc;
 #define TRY(x) do { rc = (x); if (rc) return rc; } while (0)
-  PC_CUDA_TRY(cudaMemsetAsync(c->kdone, 0, sizeof(int) * nk, s));
-  PC_CUDA_TRY(cudaMemsetAsync(c->stall_best, 0, sizeof(double) * nk, s));
-  PC_CUDA_TRY(cudaMemsetAsync(c->stall_since, 0, sizeof(int) * nk, s));
-  TRY(launch_init_guess<R>(X, nk, m, c->geom, c->Q, c->seed, s));
-  TRY(apply_R<R>(c, X, AX, OX, s));
+  PC_CUDA_TRY(cudaMemsetAsync(kdone, 0, sizeof(int) * nk, s));
+  PC_CUDA_TRY(cudaMemsetAsync(sbest, 0, sizeof(double) * nk, s));
+  PC_CUDA_TRY(cudaMemsetAsync(ssince, 0, sizeof(int) * nk, s));
+  TRY(launch_init_guess<R>(X, nk, m, c->geom, Qk, c->seed, s));
+  TRY(apply_R<R>(c, ks, X, AX, OX));
   {
     BlockList<R> A1 = {{X, nullptr, nullptr}}, B1 = {{AX, nullptr, nullptr}}, B2 = {{OX, nullptr, nullptr}};
     TRY(gram_ph<R>(c, A1, 1, B1, 1, nk, m, n3, (R)1, part, GA, s));
     TRY(gram_ph<R>(c, A1, 1, B2, 1, nk, m, n3, (R)1, part, GO, s));
-    TRY(small_rr_any<R>(c, GA, GO, m, m, c->kdone, lam, Cc, nullptr, s));
-    UpdateArgs<R> u = upd<R>(c, 1, 0, Cc, (long long)m * m, m, m);
+    TRY(small_rr_any<R>(c, nk, GA, GO, m, m, kdone, lam, Cc, nullptr, s));
+    UpdateArgs<R> u = upd<R>(c, nk, 1, 0, Cc, (long long)m * m, m, m);
     u.in[0][0] = X; u.in[1][0] = AX; u.in[2][0] = OX;
     u.out[0] = Xn; u.out[1] = AXn; u.out[2] = OXn;
     TRY(update_ph<R>(c, u, s));
@@ -668,28 +726,28 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
   }
   bool hasP = false;
   int it = 0;
-  c->unconv = nk;
+  ks.unconv = nk;
   for (it = 0; it < c->prm.max_iter; ++it) {
     // The products A X and Omega X are carried along by the same linear combinations as X;
     // their rounding drifts away from the true products.  Every c->refresh iterations they
     // are recomputed from X and the conjugate block is restarted.
     if (it > 0 && it % c->refresh == 0) {
       int sl = ph_begin(c, PH_ITER_APPLY, 8.0 * c->N * (double)c->N * 9.0 * nk * m, s);
-      TRY(apply_R<R>(c, X, AX, OX, s));
+      TRY(apply_R<R>(c, ks, X, AX, OX));
       ph_end(c, sl, s);
       hasP = false;
     }
-    TRY(launch_resnorm<R>(AX, OX, lam, nk, m, nb, n3, c->prm.tol, c->rnorm, c->active, c->kdone, c->d_unconv, s,
-                          c->stall_best, c->stall_since));
-    PC_CUDA_TRY(cudaMemcpyAsync(c->h_unconv, c->d_unconv, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TRY(launch_resnorm<R>(AX, OX, lam, nk, m, nb, n3, c->prm.tol, rnorm, active, kdone, ks.d_unconv, s, sbest,
+                          ssince));
+    PC_CUDA_TRY(cudaMemcpyAsync(ks.h_unconv, ks.d_unconv, sizeof(int), cudaMemcpyDeviceToHost, s));
     PC_CUDA_TRY(cudaStreamSynchronize(s));
-    c->unconv = *c->h_unconv;
+    ks.unconv = *ks.h_unconv;
     if (c->debug) {
       const int nv = nk * m;
       std::vector<double> h(nv);
-      cudaMemcpy(h.data(), c->rnorm, sizeof(double) * nv, cudaMemcpyDeviceToHost);
+      cudaMemcpy(h.data(), rnorm, sizeof(double) * nv, cudaMemcpyDeviceToHost);
       std::vector<int> kd(nk);
-      cudaMemcpy(kd.data(), c->kdone, sizeof(int) * nk, cudaMemcpyDeviceToHost);
+      cudaMemcpy(kd.data(), kdone, sizeof(int) * nk, cudaMemcpyDeviceToHost);
       double mx = 0, mxo = 0;
       int kmx = 0, kmxo = -1;
       for (int k = 0; k < nk; ++k)
@@ -697,24 +755,24 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
           if (h[k * m + j] > mx) { mx = h[k * m + j]; kmx = k; }
           if (!kd[k] && h[k * m + j] > mxo) { mxo = h[k * m + j]; kmxo = k; }
         }
-      fprintf(stderr, "[pc] it %d unconverged_k %d max_res %.3e at k %d; open k: max_res %.3e at k %d\n", it,
-              c->unconv, mx, kmx, mxo, kmxo);
+      fprintf(stderr, "[pc] k %d+ it %d unconverged_k %d max_res %.3e at k %d; open k: max_res %.3e at k %d\n", k0,
+              it, ks.unconv, mx, kmx + k0, mxo, kmxo < 0 ? -1 : kmxo + k0);
       const char* dk = getenv("PC_DEBUG_K");
-      if (dk) {
-        int kk = atoi(dk);
+      if (dk && atoi(dk) >= k0 && atoi(dk) < k0 + nk) {
+        int kk = atoi(dk) - k0;
         fprintf(stderr, "[pc]   k %d col res:", kk);
         for (int j = 0; j < m; ++j) fprintf(stderr, " %.1e", h[kk * m + j]);
         fprintf(stderr, "\n");
       }
     }
-    if (c->unconv == 0) break;
-    TRY(launch_precond<R>(AX, OX, lam, c->active, c->kdone, nk, m, nb, c->geom, c->Q, c->pr, c->chi_mean, Wb, s));
+    if (ks.unconv == 0) break;
+    TRY(launch_precond<R>(AX, OX, lam, active, kdone, nk, m, nb, c->geom, Qk, c->pr, c->chi_mean, Wb, s));
     // W <- W - X (OX^H W) - P (OP^H W), before the operator is applied
     {
       const int nproj = hasP ? 2 : 1;
       BlockList<R> A1 = {{OX, OP, nullptr}}, B1 = {{Wb, nullptr, nullptr}};
       TRY(gram_ph<R>(c, A1, nproj, B1, 1, nk, m, n3, (R)-1, part, Ct, s));
-      UpdateArgs<R> u = upd<R>(c, nproj + 1, 1, Ct, (long long)nproj * m * m, m, m);
+      UpdateArgs<R> u = upd<R>(c, nk, nproj + 1, 1, Ct, (long long)nproj * m * m, m, m);
       u.ntrip = 1;
       u.in[0][0] = X;
       if (hasP) { u.in[0][1] = P; u.in[0][2] = Wb; } else { u.in[0][1] = Wb; }
@@ -723,7 +781,7 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
     }
     {
       int sl = ph_begin(c, PH_ITER_APPLY, 8.0 * c->N * (double)c->N * 9.0 * nk * m, s);
-      TRY(apply_R<R>(c, Wb, AW, OW, s));
+      TRY(apply_R<R>(c, ks, Wb, AW, OW));
       ph_end(c, sl, s);
     }
     // W <- W T with T^H (W^H Omega W) T = I, dependent directions dropped
@@ -731,9 +789,9 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
       BlockList<R> A1 = {{Wb, nullptr, nullptr}}, B1 = {{OW, nullptr, nullptr}};
       TRY(gram_ph<R>(c, A1, 1, B1, 1, nk, m, n3, (R)1, part, GO, s));
       int sl = ph_begin(c, PH_SMALL, 0.0, s);
-      TRY(small_chol_any<R>(c, GO, m, Cc, s));
+      TRY(small_chol_any<R>(c, nk, GO, m, Cc, s));
       ph_end(c, sl, s);
-      UpdateArgs<R> u = upd<R>(c, 1, 0, Cc, (long long)m * m, m, m);
+      UpdateArgs<R> u = upd<R>(c, nk, 1, 0, Cc, (long long)m * m, m, m);
       u.in[0][0] = Wb; u.in[1][0] = AW; u.in[2][0] = OW;
       u.out[0] = Wb; u.out[1] = AW; u.out[2] = OW;
       TRY(update_ph<R>(c, u, s));
@@ -746,11 +804,11 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
     TRY(gram_ph<R>(c, S1, ns, SO, ns, nk, m, n3, (R)1, part, GO, s));
     {
       int sl = ph_begin(c, PH_SMALL, 0.0, s);
-      TRY(small_rr_any<R>(c, GA, GO, n, m, c->kdone, lam, Cc, Ct, s));
+      TRY(small_rr_any<R>(c, nk, GA, GO, n, m, kdone, lam, Cc, Ct, s));
       ph_end(c, sl, s);
     }
     {
-      UpdateArgs<R> u = upd<R>(c, ns, 0, Cc, (long long)n * m, m, m);
+      UpdateArgs<R> u = upd<R>(c, nk, ns, 0, Cc, (long long)n * m, m, m);
       u.in[0][0] = X; u.in[0][1] = Wb; u.in[0][2] = P;
       u.in[1][0] = AX; u.in[1][1] = AW; u.in[1][2] = AP;
       u.in[2][0] = OX; u.in[2][1] = OW; u.in[2][2] = OP;
@@ -763,12 +821,53 @@ static int run_block_iteration(pc_ctx* c, cudaStream_t s) {
     std::swap(P, Pn); std::swap(AP, APn); std::swap(OP, OPn);
     hasP = true;
   }
-  c->iterations = it;
-  // keep the final block where the FP64 step looks for it
-  C2* order[15] = {X, AX, OX, Wb, AW, OW, P, AP, OP, Xn, AXn, OXn, Pn, APn, OPn};
-  for (int i = 0; i < 15; ++i) c->blk[i] = order[i];
+  ks.iterations = it;
+  // the FP64 step reads the final block from the first block buffer
+  if (X != b[0])
+    PC_CUDA_TRY(cudaMemcpyAsync(b[0], X, sizeof(C2) * (size_t)nk * m * n3, cudaMemcpyDeviceToDevice, s));
 #undef TRY
   return PC_OK;
+}
+
+// The mixed form's block iteration on two halves of the k-points, each on its own non-blocking
+// stream and host thread.  The halves are independent problems; running them concurrently
+// lets the latency-bound projected problems of one half overlap the bandwidth- and
+// tensor-bound products of the other.  Forked from and joined back to the caller's stream
+// with events.
+static int run_split_iteration(pc_ctx* c, cudaStream_t s) {
+  if (!c->tc_ready) {
+    int rc = tc_prepare_operators(c->tc, c->W, c->T, c->cA, 1.0 / c->sO, s);
+    if (rc) return rc;
+    c->tc_ready = true;
+  }
+  PC_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
+  KSet ks[2];
+  const int h = c->nk / 2;
+  for (int i = 0; i < 2; ++i) {
+    ks[i].k0 = i ? h : 0;
+    ks[i].nk = i ? c->nk - h : h;
+    ks[i].s = c->sk[i];
+    ks[i].d_unconv = c->d_unconv + i;
+    ks[i].h_unconv = c->h_unconv + i;
+    ks[i].tc = i ? c->tc2 : c->tc;
+    PC_CUDA_TRY(cudaStreamWaitEvent(c->sk[i], c->ev_fork, 0));
+  }
+  int rc1 = PC_OK, dev = 0;
+  PC_CUDA_TRY(cudaGetDevice(&dev));
+  std::thread other([&] {
+    // a new host thread starts on device 0: adopt the caller's device first
+    if (cudaSetDevice(dev) != cudaSuccess) { rc1 = PC_ECUDA; return; }
+    rc1 = run_block_iteration<float>(c, ks[1]);
+  });
+  int rc0 = run_block_iteration<float>(c, ks[0]);
+  other.join();
+  for (int i = 0; i < 2; ++i) {
+    PC_CUDA_TRY(cudaEventRecord(c->ev_join[i], c->sk[i]));
+    PC_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[i], 0));
+  }
+  c->iterations = std::max(ks[0].iterations, ks[1].iterations);
+  c->unconv = ks[0].unconv + ks[1].unconv;
+  return rc0 ? rc0 : rc1;
 }
 
 // One FP64 Rayleigh-Ritz step on the final block: FP64 operator, FP64 Gram matrices,
@@ -795,7 +894,7 @@ static int fp64_rayleigh_ritz(pc_ctx* c, cudaStream_t s) {
   rc = launch_small_rr<double>(c->GAd, c->GOd, m, m, nk, 1e-12, nullptr, c->lamd, c->Cd, c->status, s);
   if (rc) return rc;
   // theta = X C; A theta and Omega theta for the residual report
-  UpdateArgs<double> u = upd<double>(c, 1, 0, c->Cd, (long long)m * m, m, m);
+  UpdateArgs<double> u = upd<double>(c, c->nk, 1, 0, c->Cd, (long long)m * m, m, m);
   u.in[0][0] = X; u.in[1][0] = c->AXd; u.in[2][0] = c->OXd;
   // the strain stacks Ed (6 nvec N = 2 nvec 3N entries) are free after the apply: they take
   // A theta and Omega theta for the residual report
@@ -812,7 +911,7 @@ static int fp64_rayleigh_ritz(pc_ctx* c, cudaStream_t s) {
   if (rc) return rc;
   // stresses of theta: St[s] = Sd[s] C
   for (int half = 0; half < 2; ++half) {
-    UpdateArgs<double> v = upd<double>(c, 1, 0, c->Cd, (long long)m * m, m, m);
+    UpdateArgs<double> v = upd<double>(c, c->nk, 1, 0, c->Cd, (long long)m * m, m, m);
     v.n3 = N;
     v.in_kstride = (long long)m * N;
     v.out_kstride = (long long)m * N;
@@ -834,7 +933,23 @@ extern "C" int pc_bands(pc_ctx* c, double* omega, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   PC_CUDA_TRY(cudaEventRecord(c->ev0, s));
   int sl = ph_begin(c, PH_LOOP, 0.0, s);
-  int rc = (c->prm.precision == PC_FP64) ? run_block_iteration<double>(c, s) : run_block_iteration<float>(c, s);
+  int rc;
+  const bool split = c->split && c->prm.precision == PC_MIXED && c->use_tc && c->small32 && !c->apply64 &&
+                     c->tc && c->tc2 && tc_available(c->tc) && tc_available(c->tc2) && c->nk >= 2 * kSplitMinK;
+  if (split) {
+    rc = run_split_iteration(c, s);
+  } else {
+    KSet ks;
+    ks.k0 = 0;
+    ks.nk = c->nk;
+    ks.s = s;
+    ks.d_unconv = c->d_unconv;
+    ks.h_unconv = c->h_unconv;
+    ks.tc = c->tc;
+    rc = (c->prm.precision == PC_FP64) ? run_block_iteration<double>(c, ks) : run_block_iteration<float>(c, ks);
+    c->iterations = ks.iterations;
+    c->unconv = ks.unconv;
+  }
   ph_end(c, sl, s);
   if (rc) return rc;
   sl = ph_begin(c, PH_FINAL, 0.0, s);

@@ -124,7 +124,7 @@ def test_mixed_operator_apply(B, cfg, ks):
     s.set_design(torch.from_numpy(w.rho.ravel()).cuda())
     rng = np.random.default_rng(71 + cfg)
     n3 = 3 * P.N
-    ncols = min(300, w.nk * min(w.nbands + 4, 24))
+    ncols = min(300, w.nk * s.stats().block)  # block width: bands + guard vectors
     for k in ks:
         x = rng.standard_normal((ncols, n3)) + 1j * rng.standard_normal((ncols, n3))
         ax, ox = s.apply_operator(k, torch.from_numpy(x))
