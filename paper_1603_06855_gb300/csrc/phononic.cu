@@ -29,8 +29,9 @@ std::atomic<long long> g_pc_launches{0};
 // Per-phase device timing (pc_set_profiling): event pairs recorded on the caller's stream.
 enum { PH_RR_GEMM = 0, PH_ITER_APPLY = 1, PH_SMALL = 2, PH_GRAD = 3, PH_GRAM = 4, PH_UPDATE = 5, PH_LOOP = 6,
        PH_FINAL = 7, PH_COUNT = 8 };
-// Smallest k half worth its own stream (mixed form, see pc_bands).
+// Smallest k group worth its own stream, and the most groups (mixed form, see pc_bands).
 constexpr int kSplitMinK = 16;
+constexpr int kMaxGroups = 6;
 
 struct EventPair {
   cudaEvent_t a, b;
@@ -81,10 +82,11 @@ struct pc_ctx {
   int *pairs = nullptr, *npairs = nullptr;
   double2* adj_t2 = nullptr;
   TcPlan* tc = nullptr;
-  TcPlan* tc2 = nullptr;        // workspaces of the second k half (operators shared with tc)
-  cudaStream_t sk[2] = {nullptr, nullptr};  // non-blocking streams of the two k halves
-  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+  TcPlan* tcg[kMaxGroups] = {};  // workspaces of k groups 1.. (operators shared with tc)
+  cudaStream_t sk[kMaxGroups] = {};  // non-blocking streams of the k groups
+  cudaEvent_t ev_fork = nullptr, ev_join[kMaxGroups] = {};
   int split = 1;                // PC_SPLIT=0: the block iteration of the mixed form on one stream
+  int groups = 2;               // k groups run concurrently (PC_KGROUPS, 2..kMaxGroups)
   std::mutex ph_mu;             // profiling records from the two k-half threads
   bool tc_ready = false;        // tensor-core operands prepared for the current design
   int debug = 0;  // PC_DEBUG=1 prints the residual history of the block iteration to stderr
@@ -103,6 +105,12 @@ struct pc_ctx {
   double2 *sGA = nullptr, *sGO = nullptr, *sC = nullptr, *sCP = nullptr;  // FP64 widened projected problems
   double* slam = nullptr;
 };
+
+// Number of k groups of the mixed form's block iteration for nk k-points (1: one stream).
+static int kgroups(const pc_ctx* c, int nk) {
+  if (!c->split || c->prm.precision != PC_MIXED) return 1;
+  return std::max(1, std::min(c->groups, nk / kSplitMinK));
+}
 
 // Opens a timed phase on stream s (no-op unless profiling); returns the slot index or -1.
 static int ph_begin(pc_ctx* c, int phase, double flops, cudaStream_t s, double bytes = 0.0) {
@@ -227,7 +235,8 @@ static void free_kset(pc_ctx* c) {
   dfree(c->lamd); dfree(c->lam_nd); dfree(c->rnormd); dfree(c->actived);
   dfree(c->weights); dfree(c->pairs); dfree(c->npairs); dfree(c->adj_t2);
   dfree(c->sGA); dfree(c->sGO); dfree(c->sC); dfree(c->sCP); dfree(c->slam);
-  if (c->tc2) { tc_plan_destroy(c->tc2); c->tc2 = nullptr; }
+  for (auto& t : c->tcg)
+    if (t) { tc_plan_destroy(t); t = nullptr; }
   if (c->tc) { tc_plan_destroy(c->tc); c->tc = nullptr; }
   c->nk = 0;
   c->have_bands = false;
@@ -247,7 +256,7 @@ extern "C" void pc_destroy(pc_ctx* c) {
   for (auto& e : c->ev_used) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto& e : c->ev_free) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   if (c->h_unconv) cudaFreeHost(c->h_unconv);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kMaxGroups; ++i) {
     if (c->sk[i]) cudaStreamDestroy(c->sk[i]);
     if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
   }
@@ -294,6 +303,8 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
     c->seed = sd ? strtoull(sd, nullptr, 10) : 0ull;
     const char* sp = getenv("PC_SPLIT");
     c->split = (sp && sp[0] == '0') ? 0 : 1;
+    const char* kg = getenv("PC_KGROUPS");
+    if (kg && atoi(kg) >= 2 && atoi(kg) <= kMaxGroups) c->groups = atoi(kg);
     const char* tt = getenv("PC_TC_TALL");
     g_tc_tall = (tt && tt[0] == '0') ? 0 : 1;
   }
@@ -361,14 +372,17 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
       cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
       cudaEventCreate(&c->ev_s0) != cudaSuccess || cudaEventCreate(&c->ev_s1) != cudaSuccess ||
       cudaEventCreate(&c->ev_g0) != cudaSuccess || cudaEventCreate(&c->ev_g1) != cudaSuccess ||
-      cudaMallocHost((void**)&c->h_unconv, 2 * sizeof(int)) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->sk[0], cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->sk[1], cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaMallocHost((void**)&c->h_unconv, kMaxGroups * sizeof(int)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
     pc_destroy(c);
     return PC_ECUDA;
+  }
+  for (int i = 0; i < kMaxGroups; ++i) {
+    if (cudaStreamCreateWithFlags(&c->sk[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
+      pc_destroy(c);
+      return PC_ECUDA;
+    }
   }
   *out = c;
   return PC_OK;
@@ -396,7 +410,7 @@ extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
   if (cudaMalloc(&c->lam, nvec * rsz) != cudaSuccess) { c->lam = nullptr; rc = PC_ENOMEM; }
   rc |= dalloc(&c->rnorm, nvec);
   rc |= dalloc(&c->active, nvec);
-  rc |= dalloc(&c->d_unconv, 2);
+  rc |= dalloc(&c->d_unconv, (size_t)kMaxGroups);
   rc |= dalloc(&c->kdone, (size_t)nk);
   rc |= dalloc(&c->kdone_f, (size_t)nk);
   rc |= dalloc(&c->stall_best, (size_t)nk);
@@ -430,7 +444,11 @@ extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
     c->tc_ready = false;
     if (!c->tc) rc = PC_ENOMEM;
     // second k half, run concurrently on its own stream (see pc_bands)
-    if (c->tc && nk >= 2 * kSplitMinK) c->tc2 = tc_plan_create_sharing(c->tc, (nk - nk / 2) * m, c->status);
+    const int ng = kgroups(c, nk);
+    for (int g = 1; g < ng && c->tc; ++g) {
+      const int gk = (int)(((long long)nk * (g + 1)) / ng - ((long long)nk * g) / ng);
+      c->tcg[g] = tc_plan_create_sharing(c->tc, gk * m, c->status);
+    }
   }
   if (rc != PC_OK) { free_kset(c); return PC_ENOMEM; }
   if (cudaMemcpy(c->Q, q, 3 * sizeof(double) * nk, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -829,10 +847,10 @@ static int run_block_iteration(pc_ctx* c, KSet& ks) {
   return PC_OK;
 }
 
-// The mixed form's block iteration on two halves of the k-points, each on its own non-blocking
-// stream and host thread.  The halves are independent problems; running them concurrently
-// lets the latency-bound projected problems of one half overlap the bandwidth- and
-// tensor-bound products of the other.  Forked from and joined back to the caller's stream
+// The mixed form's block iteration on groups of the k-points, each on its own non-blocking
+// stream and host thread.  The groups are independent problems; running them concurrently
+// lets the latency-bound projected problems of one group overlap the bandwidth- and
+// tensor-bound products of the others.  Forked from and joined back to the caller's stream
 // with events.
 static int run_split_iteration(pc_ctx* c, cudaStream_t s) {
   if (!c->tc_ready) {
@@ -840,34 +858,40 @@ static int run_split_iteration(pc_ctx* c, cudaStream_t s) {
     if (rc) return rc;
     c->tc_ready = true;
   }
+  const int ng = kgroups(c, c->nk);
   PC_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
-  KSet ks[2];
-  const int h = c->nk / 2;
-  for (int i = 0; i < 2; ++i) {
-    ks[i].k0 = i ? h : 0;
-    ks[i].nk = i ? c->nk - h : h;
-    ks[i].s = c->sk[i];
-    ks[i].d_unconv = c->d_unconv + i;
-    ks[i].h_unconv = c->h_unconv + i;
-    ks[i].tc = i ? c->tc2 : c->tc;
-    PC_CUDA_TRY(cudaStreamWaitEvent(c->sk[i], c->ev_fork, 0));
+  KSet ks[kMaxGroups];
+  for (int g = 0; g < ng; ++g) {
+    ks[g].k0 = (int)(((long long)c->nk * g) / ng);
+    ks[g].nk = (int)(((long long)c->nk * (g + 1)) / ng) - ks[g].k0;
+    ks[g].s = c->sk[g];
+    ks[g].d_unconv = c->d_unconv + g;
+    ks[g].h_unconv = c->h_unconv + g;
+    ks[g].tc = g ? c->tcg[g] : c->tc;
+    PC_CUDA_TRY(cudaStreamWaitEvent(c->sk[g], c->ev_fork, 0));
   }
-  int rc1 = PC_OK, dev = 0;
+  int rcs[kMaxGroups] = {}, dev = 0;
   PC_CUDA_TRY(cudaGetDevice(&dev));
-  std::thread other([&] {
-    // a new host thread starts on device 0: adopt the caller's device first
-    if (cudaSetDevice(dev) != cudaSuccess) { rc1 = PC_ECUDA; return; }
-    rc1 = run_block_iteration<float>(c, ks[1]);
-  });
-  int rc0 = run_block_iteration<float>(c, ks[0]);
-  other.join();
-  for (int i = 0; i < 2; ++i) {
-    PC_CUDA_TRY(cudaEventRecord(c->ev_join[i], c->sk[i]));
-    PC_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[i], 0));
+  std::vector<std::thread> others;
+  for (int g = 1; g < ng; ++g)
+    others.emplace_back([&, g] {
+      // a new host thread starts on device 0: adopt the caller's device first
+      if (cudaSetDevice(dev) != cudaSuccess) { rcs[g] = PC_ECUDA; return; }
+      rcs[g] = run_block_iteration<float>(c, ks[g]);
+    });
+  rcs[0] = run_block_iteration<float>(c, ks[0]);
+  for (auto& t : others) t.join();
+  c->iterations = 0;
+  c->unconv = 0;
+  int rc = PC_OK;
+  for (int g = 0; g < ng; ++g) {
+    PC_CUDA_TRY(cudaEventRecord(c->ev_join[g], c->sk[g]));
+    PC_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[g], 0));
+    c->iterations = std::max(c->iterations, ks[g].iterations);
+    c->unconv += ks[g].unconv;
+    if (!rc) rc = rcs[g];
   }
-  c->iterations = std::max(ks[0].iterations, ks[1].iterations);
-  c->unconv = ks[0].unconv + ks[1].unconv;
-  return rc0 ? rc0 : rc1;
+  return rc;
 }
 
 // One FP64 Rayleigh-Ritz step on the final block: FP64 operator, FP64 Gram matrices,
@@ -934,8 +958,9 @@ extern "C" int pc_bands(pc_ctx* c, double* omega, void* stream) {
   PC_CUDA_TRY(cudaEventRecord(c->ev0, s));
   int sl = ph_begin(c, PH_LOOP, 0.0, s);
   int rc;
-  const bool split = c->split && c->prm.precision == PC_MIXED && c->use_tc && c->small32 && !c->apply64 &&
-                     c->tc && c->tc2 && tc_available(c->tc) && tc_available(c->tc2) && c->nk >= 2 * kSplitMinK;
+  bool split = c->split && c->prm.precision == PC_MIXED && c->use_tc && c->small32 && !c->apply64 && c->tc &&
+               tc_available(c->tc) && kgroups(c, c->nk) >= 2;
+  for (int g = 1; split && g < kgroups(c, c->nk); ++g) split = c->tcg[g] && tc_available(c->tcg[g]);
   if (split) {
     rc = run_split_iteration(c, s);
   } else {
