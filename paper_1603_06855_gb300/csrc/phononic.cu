@@ -847,6 +847,8 @@ static int run_block_iteration(pc_ctx* c, KSet& ks) {
   return PC_OK;
 }
 
+static int fp64_rayleigh_ritz(pc_ctx* c, const KSet& ks);
+
 // The mixed form's block iteration on groups of the k-points, each on its own non-blocking
 // stream and host thread.  The groups are independent problems; running them concurrently
 // lets the latency-bound projected problems of one group overlap the bandwidth- and
@@ -878,8 +880,10 @@ static int run_split_iteration(pc_ctx* c, cudaStream_t s) {
       // a new host thread starts on device 0: adopt the caller's device first
       if (cudaSetDevice(dev) != cudaSuccess) { rcs[g] = PC_ECUDA; return; }
       rcs[g] = run_block_iteration<float>(c, ks[g]);
+      if (!rcs[g]) rcs[g] = fp64_rayleigh_ritz(c, ks[g]);
     });
   rcs[0] = run_block_iteration<float>(c, ks[0]);
+  if (!rcs[0]) rcs[0] = fp64_rayleigh_ritz(c, ks[0]);
   for (auto& t : others) t.join();
   c->iterations = 0;
   c->unconv = 0;
@@ -896,53 +900,67 @@ static int run_split_iteration(pc_ctx* c, cudaStream_t s) {
 
 // One FP64 Rayleigh-Ritz step on the final block: FP64 operator, FP64 Gram matrices,
 // FP64 projected eigenproblem; yields lambda, theta and the stresses of theta.
-static int fp64_rayleigh_ritz(pc_ctx* c, cudaStream_t s) {
-  const int m = c->m, nk = c->nk, N = c->N, n3 = 3 * N;
-  const long long nvec = (long long)nk * m;
+static int fp64_rayleigh_ritz(pc_ctx* c, const KSet& ks) {
+  const int m = c->m, nk = ks.nk, N = c->N, n3 = 3 * N, k0 = ks.k0;
+  cudaStream_t s = ks.s;
+  const long long nvec = (long long)nk * m, nvec_all = (long long)c->nk * m;
+  const long long vo = (long long)k0 * m;  // first vector of this subset
+  // this subset's FP64 workspaces: vectors at their global offset; strain/stress stacks
+  // [6][nvec][N] compact inside the subset's share of Ed/Sd
+  double2* Xd = c->Xd + vo * n3;
+  double2* AXd = c->AXd + vo * n3;
+  double2* OXd = c->OXd + vo * n3;
+  double2* Ed = c->Ed + 6 * vo * N;
+  double2* Sd = c->Sd + 6 * vo * N;
+  double2* GAd = c->GAd + (long long)k0 * m * m;
+  double2* GOd = c->GOd + (long long)k0 * m * m;
+  double2* Cd = c->Cd + (long long)k0 * m * m;
+  double2* gpartd = c->gpartd + 8LL * k0 * m * m;
+  double* lamd = c->lamd + vo;
   int rc;
   const double2* X;
   if (c->prm.precision == PC_MIXED) {
-    rc = launch_convert_f2d((const float2*)c->blk[0], c->Xd, nvec * n3, s);
+    rc = launch_convert_f2d((const float2*)c->blk[0] + vo * n3, Xd, nvec * n3, s);
     if (rc) return rc;
-    X = c->Xd;
+    X = Xd;
   } else {
-    X = (const double2*)c->blk[0];
+    X = (const double2*)c->blk[0] + vo * n3;
   }
-  rc = apply_fp64(c, X, c->AXd, c->OXd, (int)nvec, m, c->Q, c->cA, 1.0 / c->sO, c->Ed, c->Sd, s, PH_RR_GEMM);
+  rc = apply_fp64(c, X, AXd, OXd, (int)nvec, m, c->Q + 3 * k0, c->cA, 1.0 / c->sO, Ed, Sd, s, PH_RR_GEMM);
   if (rc) return rc;
-  BlockList<double> A1 = {{X, nullptr, nullptr}}, B1 = {{c->AXd, nullptr, nullptr}}, B2 = {{c->OXd, nullptr, nullptr}};
-  rc = launch_gram<double>(A1, 1, B1, 1, nk, m, n3, 1.0, c->gpartd, c->GAd, s);
+  BlockList<double> A1 = {{X, nullptr, nullptr}}, B1 = {{AXd, nullptr, nullptr}}, B2 = {{OXd, nullptr, nullptr}};
+  rc = launch_gram<double>(A1, 1, B1, 1, nk, m, n3, 1.0, gpartd, GAd, s);
   if (rc) return rc;
-  rc = launch_gram<double>(A1, 1, B2, 1, nk, m, n3, 1.0, c->gpartd, c->GOd, s);
+  rc = launch_gram<double>(A1, 1, B2, 1, nk, m, n3, 1.0, gpartd, GOd, s);
   if (rc) return rc;
-  rc = launch_small_rr<double>(c->GAd, c->GOd, m, m, nk, 1e-12, nullptr, c->lamd, c->Cd, c->status, s);
+  rc = launch_small_rr<double>(GAd, GOd, m, m, nk, 1e-12, nullptr, lamd, Cd, c->status, s);
   if (rc) return rc;
   // theta = X C; A theta and Omega theta for the residual report
-  UpdateArgs<double> u = upd<double>(c, c->nk, 1, 0, c->Cd, (long long)m * m, m, m);
-  u.in[0][0] = X; u.in[1][0] = c->AXd; u.in[2][0] = c->OXd;
-  // the strain stacks Ed (6 nvec N = 2 nvec 3N entries) are free after the apply: they take
+  UpdateArgs<double> u = upd<double>(c, nk, 1, 0, Cd, (long long)m * m, m, m);
+  u.in[0][0] = X; u.in[1][0] = AXd; u.in[2][0] = OXd;
+  // the strain stacks (6 nvec N = 2 nvec 3N entries) are free after the apply: they take
   // A theta and Omega theta for the residual report
-  double2* Ath = c->Ed;
-  double2* Oth = c->Ed + nvec * n3;
-  u.out[0] = c->Th;
+  double2* Ath = Ed;
+  double2* Oth = Ed + nvec * n3;
+  u.out[0] = c->Th + vo * n3;
   u.out[1] = Ath;
   u.out[2] = Oth;
   rc = launch_update<double>(u, s);
   if (rc) return rc;
-  PC_CUDA_TRY(cudaMemsetAsync(c->kdone_f, 0, sizeof(int) * nk, s));
-  rc = launch_resnorm<double>(Ath, Oth, c->lamd, nk, m, c->nb, n3, c->prm.tol, c->rnormd, c->actived,
-                              c->kdone_f, c->d_unconv, s);
+  PC_CUDA_TRY(cudaMemsetAsync(c->kdone_f + k0, 0, sizeof(int) * nk, s));
+  rc = launch_resnorm<double>(Ath, Oth, lamd, nk, m, c->nb, n3, c->prm.tol, c->rnormd + vo, c->actived + vo,
+                              c->kdone_f + k0, ks.d_unconv, s);
   if (rc) return rc;
-  // stresses of theta: St[s] = Sd[s] C
+  // stresses of theta in the global layout [6][nk m][N]: St[s] = Sd[s] C
   for (int half = 0; half < 2; ++half) {
-    UpdateArgs<double> v = upd<double>(c, c->nk, 1, 0, c->Cd, (long long)m * m, m, m);
+    UpdateArgs<double> v = upd<double>(c, nk, 1, 0, Cd, (long long)m * m, m, m);
     v.n3 = N;
     v.in_kstride = (long long)m * N;
     v.out_kstride = (long long)m * N;
     for (int t = 0; t < 3; ++t) {
       int sidx = half * 3 + t;
-      v.in[t][0] = c->Sd + (long long)sidx * nvec * N;
-      v.out[t] = c->St + (long long)sidx * nvec * N;
+      v.in[t][0] = Sd + (long long)sidx * nvec * N;
+      v.out[t] = c->St + (long long)sidx * nvec_all * N + vo * N;
     }
     rc = launch_update<double>(v, s);
     if (rc) return rc;
@@ -962,7 +980,10 @@ extern "C" int pc_bands(pc_ctx* c, double* omega, void* stream) {
                tc_available(c->tc) && kgroups(c, c->nk) >= 2;
   for (int g = 1; split && g < kgroups(c, c->nk); ++g) split = c->tcg[g] && tc_available(c->tcg[g]);
   if (split) {
+    // each k group runs its FP64 Rayleigh-Ritz step as soon as its own iteration ends
     rc = run_split_iteration(c, s);
+    ph_end(c, sl, s);
+    if (rc) return rc;
   } else {
     KSet ks;
     ks.k0 = 0;
@@ -974,13 +995,13 @@ extern "C" int pc_bands(pc_ctx* c, double* omega, void* stream) {
     rc = (c->prm.precision == PC_FP64) ? run_block_iteration<double>(c, ks) : run_block_iteration<float>(c, ks);
     c->iterations = ks.iterations;
     c->unconv = ks.unconv;
+    ph_end(c, sl, s);
+    if (rc) return rc;
+    sl = ph_begin(c, PH_FINAL, 0.0, s);
+    rc = fp64_rayleigh_ritz(c, ks);
+    ph_end(c, sl, s);
+    if (rc) return rc;
   }
-  ph_end(c, sl, s);
-  if (rc) return rc;
-  sl = ph_begin(c, PH_FINAL, 0.0, s);
-  rc = fp64_rayleigh_ritz(c, s);
-  ph_end(c, sl, s);
-  if (rc) return rc;
   rc = launch_omega(c->lamd, c->nk, c->nb, c->m, c->lref, omega, c->lam_nd, s);
   if (rc) return rc;
   PC_CUDA_TRY(cudaEventRecord(c->ev1, s));
