@@ -319,17 +319,20 @@ template <typename R> struct __align__(16) JPlane {
 // One round is one pass over A: the planes partition the index set, so A splits into 2 x 2
 // blocks (plane t1 rows, plane t2 columns), and J^H A J maps each block to L_t1 M R_t2 on its
 // own.  Only blocks with t1 <= t2 are computed (their list is built once); each writes its
-// conjugate transpose to block (t2, t1), which keeps A exactly Hermitian.  The same pass
-// rotates the column pairs of V, JV_ROWS rows per thread.
-// Scratch: pl (npairs planes), blk (npairs (npairs + 1) / 2 ints), red (2 blockDim).
+// conjugate transpose to block (t2, t1), which keeps A exactly Hermitian.  The planes of the
+// next round depend on A only, so they are computed (by npairs threads) while the other
+// threads rotate the column pairs of V for the current round, JV_ROWS rows per thread; the
+// plane parameters are double-buffered by round.
+// Scratch: pl (2 x 64 planes), blk (npairs (npairs + 1) / 2 ints), red (2 blockDim).
 #define JV_ROWS 8
 template <typename R>
 __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V, int n, int ld, int nx, int max_sweeps,
                        JPlane<R>* pl, int* blk, R* red, const int* drop) {
   typedef typename cplx_t<R>::type C2;
-  __shared__ int rotated;
+  __shared__ int rot[2];  // a rotation happened in the sweep (by sweep parity)
   const int npad = n + (n & 1);
   const int npairs = npad / 2;
+  const int nrounds = npad - 1;
   const R eps = SmallEps<R>::v;
   // exact Hermitian start: the triangular reductions leave rounding-level asymmetry
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
@@ -353,92 +356,100 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
   for (int i = threadIdx.x; i < nx; i += blockDim.x)
     if (!drop[i]) amax = fmax(amax, fabs(A[i * ld + i].x));
   red[threadIdx.x] = amax;
+  if (threadIdx.x == 0) { rot[0] = 0; rot[1] = 0; }
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
     __syncthreads();
   }
   const R floor_abs = eps * red[0];
-  __syncthreads();
   const int nch = (n + JV_ROWS - 1) / JV_ROWS;
   const int nV = npairs * nch;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) rotated = 0;
-    __syncthreads();
-    for (int round = 0; round < npad - 1; ++round) {
-      for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
-        int a = (t == 0) ? 0 : ((t - 1 + round) % (npad - 1)) + 1;
-        int b = ((npad - 1 - t - 1 + round) % (npad - 1)) + 1;
-        int p = min(a, b), q = max(a, b);
-        R c = 1;
-        C2 sp = mk<R>(0, 0);
-        if (q < n && !drop[p] && !drop[q]) {
-          C2 apq = A[p * ld + q];
-          R beta = sqrt(apq.x * apq.x + apq.y * apq.y);
-          R app = A[p * ld + p].x, aqq = A[q * ld + q].x;
-          if (beta > eps * sqrt(fabs(app) * fabs(aqq)) + floor_abs) {
-            R tau = (aqq - app) / (2 * beta);
-            R tt = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
-            c = (R)1 / sqrt((R)1 + tt * tt);
-            R sn = tt * c;
-            sp = mk<R>(sn * apq.x / beta, sn * apq.y / beta);
-            rotated = 1;
-          }
-        }
-        JPlane<R> w;
-        w.c = c;
-        w.s = sp;
-        w.pq = p | (q << 16);
-        pl[t] = w;
+  // rotation of plane t in the given round, from the current A
+  auto plane = [&](int round, int t, JPlane<R>* dst, int* flag) {
+    int a = (t == 0) ? 0 : ((t - 1 + round) % nrounds) + 1;
+    int b = ((nrounds - t - 1 + round) % nrounds) + 1;
+    int p = min(a, b), q = max(a, b);
+    R c = 1;
+    C2 sp = mk<R>(0, 0);
+    if (q < n && !drop[p] && !drop[q]) {
+      C2 apq = A[p * ld + q];
+      R beta = sqrt(apq.x * apq.x + apq.y * apq.y);
+      R app = A[p * ld + p].x, aqq = A[q * ld + q].x;
+      if (beta > eps * sqrt(fabs(app) * fabs(aqq)) + floor_abs) {
+        R tau = (aqq - app) / (2 * beta);
+        R tt = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
+        c = (R)1 / sqrt((R)1 + tt * tt);
+        R sn = tt * c;
+        sp = mk<R>(sn * apq.x / beta, sn * apq.y / beta);
+        *flag = 1;
       }
-      __syncthreads();
-      for (int e = threadIdx.x; e < nA + nV; e += blockDim.x) {
-        if (e < nA) {
-          // block (t1, t2) of A: rows p1, q1 and columns p2, q2
-          const int tt12 = blk[e];
-          const int t1 = tt12 & 255, t2 = tt12 >> 8;
-          const JPlane<R> w1 = pl[t1], w2 = pl[t2];
-          const C2 s1 = w1.s, s2 = w2.s;
-          const bool a1 = (s1.x != 0 || s1.y != 0), a2 = (s2.x != 0 || s2.y != 0);
-          if (!a1 && !a2) continue;
-          const R c1 = w1.c, c2 = w2.c;
-          const int p1 = w1.pq & 0xffff, q1 = w1.pq >> 16, p2 = w2.pq & 0xffff, q2 = w2.pq >> 16;
-          const bool v1 = q1 < n, v2 = q2 < n;
-          const C2 z = mk<R>(0, 0);
-          C2 m00 = A[p1 * ld + p2];
-          C2 m01 = v2 ? A[p1 * ld + q2] : z;
-          C2 m10 = v1 ? A[q1 * ld + p2] : z;
-          C2 m11 = (v1 && v2) ? A[q1 * ld + q2] : z;
-          // columns (plane t2): col_p <- c col_p - conj(s) col_q, col_q <- s col_p + c col_q
-          const C2 s2c = cconj(s2);
-          C2 y00 = csub(cscale(m00, c2), cmul(s2c, m01)), y01 = cadd(cmul(s2, m00), cscale(m01, c2));
-          C2 y10 = csub(cscale(m10, c2), cmul(s2c, m11)), y11 = cadd(cmul(s2, m10), cscale(m11, c2));
-          // rows (plane t1): row_p <- c row_p - s row_q, row_q <- conj(s) row_p + c row_q
-          const C2 s1c = cconj(s1);
-          m00 = csub(cscale(y00, c1), cmul(s1, y10));
-          m01 = csub(cscale(y01, c1), cmul(s1, y11));
-          m10 = cadd(cmul(s1c, y00), cscale(y10, c1));
-          m11 = cadd(cmul(s1c, y01), cscale(y11, c1));
-          if (t1 == t2) {  // the rotated plane itself: its off-diagonal pair is annihilated
-            A[p1 * ld + p1] = mk<R>(m00.x, 0);
-            if (v1) {
-              A[q1 * ld + q1] = mk<R>(m11.x, 0);
-              A[p1 * ld + q1] = z;
-              A[q1 * ld + p1] = z;
-            }
-          } else {
-            A[p1 * ld + p2] = m00;
-            A[p2 * ld + p1] = cconj(m00);
-            if (v2) { A[p1 * ld + q2] = m01; A[q2 * ld + p1] = cconj(m01); }
-            if (v1) { A[q1 * ld + p2] = m10; A[p2 * ld + q1] = cconj(m10); }
-            if (v1 && v2) { A[q1 * ld + q2] = m11; A[q2 * ld + q1] = cconj(m11); }
+    }
+    JPlane<R> w;
+    w.c = c;
+    w.s = sp;
+    w.pq = p | (q << 16);
+    dst[t] = w;
+  };
+  for (int t = threadIdx.x; t < npairs; t += blockDim.x) plane(0, t, pl, &rot[0]);
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int round = 0; round < nrounds; ++round) {
+      const int g = sweep * nrounds + round;
+      const JPlane<R>* cur = pl + (g & 1) * 64;
+      JPlane<R>* nxt = pl + ((g + 1) & 1) * 64;
+      // A <- J^H A J: block (t1, t2), rows p1, q1 and columns p2, q2
+      for (int e = threadIdx.x; e < nA; e += blockDim.x) {
+        const int tt12 = blk[e];
+        const int t1 = tt12 & 255, t2 = tt12 >> 8;
+        const JPlane<R> w1 = cur[t1], w2 = cur[t2];
+        const C2 s1 = w1.s, s2 = w2.s;
+        const bool a1 = (s1.x != 0 || s1.y != 0), a2 = (s2.x != 0 || s2.y != 0);
+        if (!a1 && !a2) continue;
+        const R c1 = w1.c, c2 = w2.c;
+        const int p1 = w1.pq & 0xffff, q1 = w1.pq >> 16, p2 = w2.pq & 0xffff, q2 = w2.pq >> 16;
+        const bool v1 = q1 < n, v2 = q2 < n;
+        const C2 z = mk<R>(0, 0);
+        C2 m00 = A[p1 * ld + p2];
+        C2 m01 = v2 ? A[p1 * ld + q2] : z;
+        C2 m10 = v1 ? A[q1 * ld + p2] : z;
+        C2 m11 = (v1 && v2) ? A[q1 * ld + q2] : z;
+        // columns (plane t2): col_p <- c col_p - conj(s) col_q, col_q <- s col_p + c col_q
+        const C2 s2c = cconj(s2);
+        C2 y00 = csub(cscale(m00, c2), cmul(s2c, m01)), y01 = cadd(cmul(s2, m00), cscale(m01, c2));
+        C2 y10 = csub(cscale(m10, c2), cmul(s2c, m11)), y11 = cadd(cmul(s2, m10), cscale(m11, c2));
+        // rows (plane t1): row_p <- c row_p - s row_q, row_q <- conj(s) row_p + c row_q
+        const C2 s1c = cconj(s1);
+        m00 = csub(cscale(y00, c1), cmul(s1, y10));
+        m01 = csub(cscale(y01, c1), cmul(s1, y11));
+        m10 = cadd(cmul(s1c, y00), cscale(y10, c1));
+        m11 = cadd(cmul(s1c, y01), cscale(y11, c1));
+        if (t1 == t2) {  // the rotated plane itself: its off-diagonal pair is annihilated
+          A[p1 * ld + p1] = mk<R>(m00.x, 0);
+          if (v1) {
+            A[q1 * ld + q1] = mk<R>(m11.x, 0);
+            A[p1 * ld + q1] = z;
+            A[q1 * ld + p1] = z;
           }
         } else {
+          A[p1 * ld + p2] = m00;
+          A[p2 * ld + p1] = cconj(m00);
+          if (v2) { A[p1 * ld + q2] = m01; A[q2 * ld + p1] = cconj(m01); }
+          if (v1) { A[q1 * ld + p2] = m10; A[p2 * ld + q1] = cconj(m10); }
+          if (v1 && v2) { A[q1 * ld + q2] = m11; A[q2 * ld + q1] = cconj(m11); }
+        }
+      }
+      __syncthreads();
+      // planes of the next round (the first npairs threads) while the others rotate V
+      if ((int)threadIdx.x < npairs) {
+        const bool last = round + 1 == nrounds;
+        plane(last ? 0 : round + 1, threadIdx.x, nxt, &rot[(sweep + (last ? 1 : 0)) & 1]);
+      } else {
+        for (int e2 = threadIdx.x - npairs; e2 < nV; e2 += blockDim.x - npairs) {
           // rows c0, c0 + nch, c0 + 2 nch, ... of V, column pair of plane t: V <- V J
           // (neighbouring lanes take neighbouring rows: distinct banks with the odd stride)
-          const int e2 = e - nA;
           const int t = e2 / nch, c0 = e2 - t * nch;
-          const JPlane<R> w = pl[t];
+          const JPlane<R> w = cur[t];
           const C2 sp = w.s;
           if (sp.x == 0 && sp.y == 0) continue;
           const int p = w.pq & 0xffff, q = w.pq >> 16;
@@ -454,8 +465,11 @@ __device__ void jacobi(typename cplx_t<R>::type* A, typename cplx_t<R>::type* V,
       }
       __syncthreads();
     }
-    bool done = (rotated == 0);
+    // sweep finished: stop if it rotated nothing (the planes already computed for the next
+    // sweep came from an unchanged A and are dropped)
+    const bool done = (rot[sweep & 1] == 0);
     __syncthreads();
+    if (threadIdx.x == 0) rot[sweep & 1] = 0;  // reused by sweep + 2
     if (done) break;
   }
   __syncthreads();
@@ -467,7 +481,7 @@ template <typename R> struct SmallSmem {
   static size_t bytes(int n) {
     typedef typename cplx_t<R>::type C2;
     const int L = ld(n);
-    return sizeof(C2) * (2 * (size_t)n * L + n) + sizeof(JPlane<R>) * 64 + sizeof(R) * (2 * n + 2 * SMALL_THREADS) +
+    return sizeof(C2) * (2 * (size_t)n * L + n) + sizeof(JPlane<R>) * 128 + sizeof(R) * (2 * n + 2 * SMALL_THREADS) +
            sizeof(int) * (2 * n + 64 * 65 / 2 + 16);
   }
 };
@@ -483,8 +497,8 @@ __global__ __launch_bounds__(SMALL_THREADS) void k_small_rr(const typename cplx_
   const int ld = n + ((n & 1) ? 0 : 1);
   C2* A = (C2*)smem;                 // n*ld
   C2* B = A + n * ld;                // n*ld
-  JPlane<R>* pl = (JPlane<R>*)(B + n * ld);  // 64 planes
-  C2* tmp = (C2*)(pl + 64);          // n
+  JPlane<R>* pl = (JPlane<R>*)(B + n * ld);  // 2 x 64 planes
+  C2* tmp = (C2*)(pl + 128);         // n
   R* D = (R*)(tmp + n);              // n
   R* ev = D + n;                     // n
   R* red = ev + n;                   // 2 * SMALL_THREADS
