@@ -15,10 +15,10 @@
 
 int g_acc64 = 0;  // experiment switch: FP64 accumulation in the FP32 Gram and update kernels
 
-// G_part[k][split] = A^H B over one row range.  Shared tiles are double-buffered: the next
+// G_part[k][split] = A^H B over one row range; each of the 16 x 16 threads holds TILE x TILE outputs.  Shared tiles are double-buffered: the next
 // tile of GRAM_ROWS rows (16 in FP32, 8 in FP64: 37 KB of static shared memory either way)
 // is fetched into registers while the current one is multiplied.
-template <typename R, typename RA>
+template <typename R, typename RA, int TILE>
 __global__ __launch_bounds__(256) void k_gram(BlockList<R> A, int na, BlockList<R> B, int nbk, int m, int n3,
                                               typename cplx_t<R>::type* __restrict__ part) {
   typedef typename cplx_t<R>::type C2;
@@ -59,11 +59,11 @@ __global__ __launch_bounds__(256) void k_gram(BlockList<R> A, int na, BlockList<
       if (u < nlb && t < GRAM_ROWS * cb) sB[buf][(t % GRAM_ROWS) * GRAM_LD + t / GRAM_ROWS] = rb[u];
     }
   };
-  CA acc[5][5];
+  CA acc[TILE][TILE];
 #pragma unroll
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < TILE; ++i)
 #pragma unroll
-    for (int j = 0; j < 5; ++j) acc[i][j] = mk<RA>(0, 0);
+    for (int j = 0; j < TILE; ++j) acc[i][j] = mk<RA>(0, 0);
   int buf = 0;
   if (r_begin < r_end) {
     fetch(r_begin);
@@ -77,15 +77,15 @@ __global__ __launch_bounds__(256) void k_gram(BlockList<R> A, int na, BlockList<
     const C2* b_t = sB[buf];
 #pragma unroll 4
     for (int rr = 0; rr < GRAM_ROWS; ++rr) {
-      C2 a[5], b[5];
+      C2 a[TILE], b[TILE];
 #pragma unroll
-      for (int i = 0; i < 5; ++i) { int c = tx + 16 * i; a[i] = c < ca ? a_t[rr * GRAM_LD + c] : mk<R>(0, 0); }
+      for (int i = 0; i < TILE; ++i) { int c = tx + 16 * i; a[i] = c < ca ? a_t[rr * GRAM_LD + c] : mk<R>(0, 0); }
 #pragma unroll
-      for (int j = 0; j < 5; ++j) { int c = ty + 16 * j; b[j] = c < cb ? b_t[rr * GRAM_LD + c] : mk<R>(0, 0); }
+      for (int j = 0; j < TILE; ++j) { int c = ty + 16 * j; b[j] = c < cb ? b_t[rr * GRAM_LD + c] : mk<R>(0, 0); }
 #pragma unroll
-      for (int i = 0; i < 5; ++i)
+      for (int i = 0; i < TILE; ++i)
 #pragma unroll
-        for (int j = 0; j < 5; ++j) cfmac(acc[i][j], mk<RA>(a[i].x, a[i].y), mk<RA>(b[j].x, b[j].y));
+        for (int j = 0; j < TILE; ++j) cfmac(acc[i][j], mk<RA>(a[i].x, a[i].y), mk<RA>(b[j].x, b[j].y));
     }
     if (more) stash(buf ^ 1);
     __syncthreads();
@@ -93,9 +93,9 @@ __global__ __launch_bounds__(256) void k_gram(BlockList<R> A, int na, BlockList<
   }
   C2* out = part + ((long long)k * GRAM_SPLIT + split) * ca * cb;
 #pragma unroll
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < TILE; ++i)
 #pragma unroll
-    for (int j = 0; j < 5; ++j) {
+    for (int j = 0; j < TILE; ++j) {
       int a_ = tx + 16 * i, b_ = ty + 16 * j;
       if (a_ < ca && b_ < cb) out[a_ * cb + b_] = mk<R>((R)acc[i][j].x, (R)acc[i][j].y);
     }
@@ -129,8 +129,15 @@ int launch_gram(BlockList<R> A, int na, BlockList<R> B, int nbk, int nk, int m, 
     if (g_tc_tall && status && !g_acc64) return launch_gram_tc(A.p, na, B.p, nbk, nk, m, n3, scale, part, GRAM_SPLIT, G, status, s);
   }
   dim3 grid(nk, GRAM_SPLIT);
-  if (g_acc64) k_gram<R, double><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
-  else k_gram<R, R><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
+  // 16 x 16 threads, TILE x TILE outputs each: 2 x 2 covers up to 32 columns per side
+  const bool small = na * m <= 32 && nbk * m <= 32;
+  if (g_acc64) {
+    if (small) k_gram<R, double, 2><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
+    else k_gram<R, double, 5><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
+  } else {
+    if (small) k_gram<R, R, 2><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
+    else k_gram<R, R, 5><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
+  }
   PC_LAUNCH_CHECK();
   int nel = na * m * nbk * m;
   dim3 g2(cdiv(nel, 256), nk);
