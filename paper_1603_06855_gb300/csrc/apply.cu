@@ -265,7 +265,9 @@ template int launch_resnorm<float>(const float2*, const float2*, const float*, i
 
 // Preconditioned residual W = P_q (A x - lambda Omega x) with P_q the inverse of a shifted
 // homogeneous Christoffel operator a I + b K K^T of a reference medium (mean chi):
-// (a I + b K K^T)^-1 = (I - b/(a + b|K|^2) K K^T) / a.  Converged columns get W = 0.
+// (a I + b K K^T)^-1 = (I - b/(a + b|K|^2) K K^T) / a, a = mu |K|^2 + s rho sigma, b = lambda + mu,
+// sigma the largest wanted Ritz value at the k-point and s the weight of the mass term.
+// Converged columns get W = 0.
 template <typename R>
 __global__ void k_precond(const typename cplx_t<R>::type* __restrict__ AX, const typename cplx_t<R>::type* __restrict__ OX,
                           const R* __restrict__ lam, const int* __restrict__ active, const int* __restrict__ kdone,
@@ -283,12 +285,21 @@ __global__ void k_precond(const typename cplx_t<R>::type* __restrict__ AX, const
     return;
   }
   const double cm = *chi_mean;
-  const R lam_r = (R)(pr.lam0 + cm * (pr.lam1 - pr.lam0));
-  const R mu_r = (R)(pr.mu0 + cm * (pr.mu1 - pr.mu0));
+  double lam_d, mu_d;
+  if (pr.ref_mode == 1) {  // compliance linear in chi: bulk 1/(3 f1), shear 1/(2 f2)
+    const double f1 = pr.f1_0 + cm * (pr.f1_1 - pr.f1_0), f2 = pr.f2_0 + cm * (pr.f2_1 - pr.f2_0);
+    mu_d = 0.5 / f2;
+    lam_d = 1.0 / (3.0 * f1) - 2.0 * mu_d / 3.0;
+  } else {
+    lam_d = pr.lam0 + cm * (pr.lam1 - pr.lam0);
+    mu_d = pr.mu0 + cm * (pr.mu1 - pr.mu0);
+  }
+  const R lam_r = (R)lam_d;
+  const R mu_r = (R)mu_d;
   const R rho_r = (R)(pr.rho0 + cm * (pr.rho1 - pr.rho0));
   R sig = 0;
   for (int j = 0; j < nb; ++j) sig = fmax(sig, lam[k * m + j]);
-  sig = fmax(sig, (R)1e-6);
+  sig = fmax(sig, (R)1e-6) * (R)pr.shift_scale;
   double Kd[3];
   kvec(g, Q, k, q, Kd);
   const R K0 = (R)Kd[0], K1 = (R)Kd[1], K2 = (R)Kd[2];

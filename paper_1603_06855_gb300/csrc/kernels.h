@@ -57,8 +57,11 @@ struct PrecConsts {
 };
 struct PrecRef {  // reference medium from the mean of chi (device scalar)
   double lam0, lam1, mu0, mu1, rho0, rho1;
+  double f1_0, f1_1, f2_0, f2_1;  // compliance moduli (1-2nu)/E, (1+nu)/E of the phases
   double two_pi_sq_V_over_sA;
   double half_lref_V_over_sA;
+  int ref_mode;       // 0: Lame constants linear in chi; 1: compliance linear in chi (the material law)
+  double shift_scale; // weight of the mass term rho sigma
 };
 template <typename R>
 int launch_resnorm(const typename cplx_t<R>::type* AX, const typename cplx_t<R>::type* OX,

@@ -345,6 +345,20 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
   lame(p->phase1, &c->pr.lam1, &c->pr.mu1);
   c->pr.rho0 = p->phase0.rho;
   c->pr.rho1 = p->phase1.rho;
+  c->pr.f1_0 = (1.0 - 2.0 * p->phase0.nu) / p->phase0.E;
+  c->pr.f1_1 = (1.0 - 2.0 * p->phase1.nu) / p->phase1.E;
+  c->pr.f2_0 = (1.0 + p->phase0.nu) / p->phase0.E;
+  c->pr.f2_1 = (1.0 + p->phase1.nu) / p->phase1.E;
+  {
+    // Reference medium of the preconditioner: the homogeneous material at the mean chi, with
+    // compliance linear in chi as in the material law (PC_PREC_REF=0: Lame constants linear in
+    // chi, a stiffer medium); its mass term rho sigma weighted by 0.25 (PC_PREC_SHIFT).  On the
+    // FCC N = 729 designs this pair took 12 % fewer block iterations than (0, 1).
+    const char* rm = getenv("PC_PREC_REF");
+    c->pr.ref_mode = (rm && rm[0] == '0') ? 0 : 1;
+    const char* sh = getenv("PC_PREC_SHIFT");
+    c->pr.shift_scale = (sh && atof(sh) > 0) ? atof(sh) : 0.25;
+  }
   c->pr.two_pi_sq_V_over_sA = two_pi * two_pi * c->V / c->sA;
   c->pr.half_lref_V_over_sA = 0.5 * c->lref * c->V / c->sA;
 
