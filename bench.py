@@ -259,7 +259,7 @@ def main():
         ck = clocks.stop()
         ms = e0.elapsed_time(e1)
         st = s.stats()
-        run.last = ((warmup + steps - 1) % len(rhos), omega)
+        run.last = ((warmup + steps - 1) % len(rhos), omega, grad)
         return s, ms, st, ck
 
     # ---- mixed form (headline) ----
@@ -352,11 +352,15 @@ def main():
                 "mixed_over_fp64": value / world / v64}
         # accuracy of the headline form: mixed and FP64 frequencies of the same design (untimed);
         # relative to max(w_fp64, 0.05 max w_fp64), Gamma zero modes (w < 1e-4 max w) left out
-        d64, om64 = run.last
+        d64, om64, g64 = run.last
         om_mx = torch.empty_like(om64)
+        g_mx = torch.empty_like(g64)
+        gap_mx = torch.empty(1, dtype=torch.float64, device=dev)
         s_mx.set_design(rhos[d64])
         s_mx.bands(out=om_mx)
+        s_mx.gap_and_grad(mode=B.PC_GRAD_ALLBANDS, weights=wts, gap_out=gap_mx, grad_out=g_mx)
         torch.cuda.synchronize(dev)
+        fp64["grad_rel_l2_mixed_vs_fp64"] = float(torch.linalg.norm(g_mx - g64) / torch.linalg.norm(g64))
         a, b = om_mx.cpu().numpy(), om64.cpu().numpy()
         err = np.abs(a - b) / np.maximum(b, 0.05 * b.max())
         err[b < 1e-4 * b.max()] = 0.0

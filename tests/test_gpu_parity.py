@@ -266,3 +266,37 @@ def test_autograd_function(B):
     assert abs(g.item() - r.gap) <= 1e-8
     assert np.linalg.norm(rho.grad.cpu().numpy() - g_ref) <= 1e-6 * np.linalg.norm(g_ref)
     s.close()
+
+
+def test_gap_gradient_central_differences(B):
+    """Central finite differences of the GPU gap itself (FP64 form, SC 16^3 random design, gap
+    between bands 6 and 7 over 30 k): no symmetry, so the bands at the extremal k-points are
+    non-degenerate and the gap is smooth there.  Step 1e-4 in rho on the eight voxels with the
+    largest sensitivities and two random ones; agreement within 1e-4 relative (truncation
+    O(h^2) and the 1e-8 residual target keep the difference quotient to ~1e-7)."""
+    from paper_1603_06855_gb300.solver import BandSolver
+    w = wl.config1()
+    s = BandSolver.from_workload(w)
+    rho = torch.from_numpy(w.rho.ravel()).cuda()
+    s.set_design(rho)
+    s.bands()
+    _, grad = s.gap_and_grad(6)
+    grad = grad.cpu().numpy().ravel()
+    rng = np.random.default_rng(1606)
+    idx = list(np.argsort(-np.abs(grad))[:8]) + list(rng.choice(grad.size, 2, replace=False))
+    h = 1e-4
+    fd = []
+    for e in idx:
+        vals = []
+        for sgn in (1.0, -1.0):
+            r = rho.clone()
+            r[e] += sgn * h
+            s.set_design(r)
+            s.bands()
+            gp, _ = s.gap_and_grad(6)
+            vals.append(gp.item())
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    fd = np.array(fd)
+    g = grad[idx]
+    assert np.all(np.abs(fd - g) <= 1e-4 * np.abs(g).max()), (fd, g)
+    s.close()
