@@ -14,9 +14,11 @@
 // GEMM kernel (sm_103a): C[col][row] = sum_k A[row][k] B[col][k], both operands K-major
 // bf16 in global memory, loaded by TMA (128-byte swizzle) into a 2-stage shared-memory
 // ring; one thread issues tcgen05.mma (kind::f16, M = 128, N = 128, K = 16) into an FP32
-// accumulator in tensor memory; four epilogue warps read it back with tcgen05.ld and store
-// FP32.  Warp 0 produces, warp 1 issues MMAs, warps 2-5 drain.  Every mbarrier wait is
+// accumulator in tensor memory (two halves, alternating by tile); four epilogue warps read it
+// back with tcgen05.ld and store FP32.  Warp 0 produces, warp 1 issues MMAs, warps 2-5 drain;
+// the kernel is persistent, one CTA per SM walking the output tiles.  Every mbarrier wait is
 // bounded: on expiry the kernel records PC_ETIMEOUT in the status word and stops waiting.
+#include <algorithm>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include "gemm_tc.h"
@@ -37,36 +39,43 @@ constexpr int SMEM_BYTES = TC_STAGES * STAGE_BYTES + 1024 /* barriers */ + 1024 
 // Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N = TC_BN.
 __host__ __device__ constexpr uint32_t idesc_bf16() { return idesc_bf16_n(TC_BN); }
 
+// Persistent: each CTA walks the output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (M-fastest, so CTAs working at the same time share the B column tile in L2).  The stage
+// ring runs on across tiles, and the accumulator alternates between two 128-column halves of
+// tensor memory, so the epilogue warps drain tile i while the MMAs of tile i + 1 run.
 __global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUtensorMap tA_hi,
                                                     const __grid_constant__ CUtensorMap tA_mid,
                                                     const __grid_constant__ CUtensorMap tA_lo,
                                                     const __grid_constant__ CUtensorMap tB_hi,
                                                     const __grid_constant__ CUtensorMap tB_mid,
                                                     const __grid_constant__ CUtensorMap tB_lo, int num_kb, int col_base,
-                                                    int ncols, int m_valid, float* __restrict__ C, long long ldc,
-                                                    int* status) {
+                                                    int ncols, int m_valid, int mtiles, int ntiles,
+                                                    float* __restrict__ C, long long ldc, int* status) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* gbase = smem_raw + (base - raw);
   const uint32_t bars = base + TC_STAGES * STAGE_BYTES;
-  // barrier layout: full[s] at bars + 8 s, empty[s] at bars + 64 + 8 s, accum at bars + 128, tmem slot at bars + 192
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + TC_STAGES * STAGE_BYTES + 192);
+  // barriers: full[s] +8s, empty[s] +64+8s, tfull[b] +128+8b, tempty[b] +160+8b, done +192; tmem slot +256
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + TC_STAGES * STAGE_BYTES + 256);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * TC_BM;
-  const int n0 = blockIdx.y * TC_BN;
+  const int tiles = mtiles * ntiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(bars + 8 * s, 1);
       mbar_init(bars + 64 + 8 * s, 1);
     }
-    mbar_init(bars + 128, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bars + 128 + 8 * b, 1);
+      mbar_init(bars + 160 + 8 * b, 128);
+    }
+    mbar_init(bars + 192, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)TC_BN)
+                 "r"((uint32_t)(2 * TC_BN))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -77,71 +86,95 @@ __global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUte
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int kb = 0; kb < num_kb; ++kb) {
-        const int s = kb % TC_STAGES;
-        const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
-        if (!mbar_wait(bars + 64 + 8 * s, ph ^ 1u, status)) break;
-        const uint32_t st = base + s * STAGE_BYTES;
-        mbar_expect_tx(bars + 8 * s, STAGE_BYTES);
-        tma_load_2d(st, &tA_hi, bars + 8 * s, kb * TC_BK, m0);
-        tma_load_2d(st + A_TILE, &tA_mid, bars + 8 * s, kb * TC_BK, m0);
-        tma_load_2d(st + 2 * A_TILE, &tA_lo, bars + 8 * s, kb * TC_BK, m0);
-        tma_load_2d(st + 3 * A_TILE, &tB_hi, bars + 8 * s, kb * TC_BK, col_base + n0);
-        tma_load_2d(st + 3 * A_TILE + B_TILE, &tB_mid, bars + 8 * s, kb * TC_BK, col_base + n0);
-        tma_load_2d(st + 3 * A_TILE + 2 * B_TILE, &tB_lo, bars + 8 * s, kb * TC_BK, col_base + n0);
+      long long it = 0;  // stage counter across tiles
+      bool ok = true;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const int m0 = (t % mtiles) * TC_BM, n0 = (t / mtiles) * TC_BN;
+        for (int kb = 0; kb < num_kb; ++kb, ++it) {
+          const int s = (int)(it % TC_STAGES);
+          const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+          if (!(ok = mbar_wait(bars + 64 + 8 * s, ph ^ 1u, status))) break;
+          const uint32_t st = base + s * STAGE_BYTES;
+          mbar_expect_tx(bars + 8 * s, STAGE_BYTES);
+          tma_load_2d(st, &tA_hi, bars + 8 * s, kb * TC_BK, m0);
+          tma_load_2d(st + A_TILE, &tA_mid, bars + 8 * s, kb * TC_BK, m0);
+          tma_load_2d(st + 2 * A_TILE, &tA_lo, bars + 8 * s, kb * TC_BK, m0);
+          tma_load_2d(st + 3 * A_TILE, &tB_hi, bars + 8 * s, kb * TC_BK, col_base + n0);
+          tma_load_2d(st + 3 * A_TILE + B_TILE, &tB_mid, bars + 8 * s, kb * TC_BK, col_base + n0);
+          tma_load_2d(st + 3 * A_TILE + 2 * B_TILE, &tB_lo, bars + 8 * s, kb * TC_BK, col_base + n0);
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16();
+      long long it = 0;
       bool ok = true;
-      for (int kb = 0; kb < num_kb && ok; ++kb) {
-        const int s = kb % TC_STAGES;
-        const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
-        ok = mbar_wait(bars + 8 * s, ph, status);
-        if (!ok) break;
+      int tl = 0;  // local tile index
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
+        const int b = tl & 1;
+        // accumulator half b must have been drained (its use tl / 2 - 1)
+        if (!(ok = mbar_wait(bars + 160 + 8 * b, ((uint32_t)(tl >> 1) & 1u) ^ 1u, status))) break;
         tc_fence_after();
-        const uint32_t st = base + s * STAGE_BYTES;
-        const uint64_t ah = sw128_desc(st), am = sw128_desc(st + A_TILE), al = sw128_desc(st + 2 * A_TILE);
-        const uint64_t bh = sw128_desc(st + 3 * A_TILE), bm = sw128_desc(st + 3 * A_TILE + B_TILE);
-        const uint64_t bl = sw128_desc(st + 3 * A_TILE + 2 * B_TILE);
+        const uint32_t d = tmem + (uint32_t)(b * TC_BN);
+        for (int kb = 0; kb < num_kb; ++kb, ++it) {
+          const int s = (int)(it % TC_STAGES);
+          const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+          if (!(ok = mbar_wait(bars + 8 * s, ph, status))) break;
+          tc_fence_after();
+          const uint32_t st = base + s * STAGE_BYTES;
+          const uint64_t ah = sw128_desc(st), am = sw128_desc(st + A_TILE), al = sw128_desc(st + 2 * A_TILE);
+          const uint64_t bh = sw128_desc(st + 3 * A_TILE), bm = sw128_desc(st + 3 * A_TILE + B_TILE);
+          const uint64_t bl = sw128_desc(st + 3 * A_TILE + 2 * B_TILE);
 #pragma unroll
-        for (int kk = 0; kk < TC_BK / 16; ++kk) {
-          const uint64_t off = (uint64_t)((kk * 32) >> 4);  // 16 bf16 = 32 bytes along K
-          mma_bf16(tmem, ah + off, bh + off, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-          mma_bf16(tmem, ah + off, bm + off, idesc, 1u);
-          mma_bf16(tmem, am + off, bh + off, idesc, 1u);
-          mma_bf16(tmem, ah + off, bl + off, idesc, 1u);
-          mma_bf16(tmem, am + off, bm + off, idesc, 1u);
-          mma_bf16(tmem, al + off, bh + off, idesc, 1u);
+          for (int kk = 0; kk < TC_BK / 16; ++kk) {
+            const uint64_t off = (uint64_t)((kk * 32) >> 4);  // 16 bf16 = 32 bytes along K
+            mma_bf16(d, ah + off, bh + off, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            mma_bf16(d, ah + off, bm + off, idesc, 1u);
+            mma_bf16(d, am + off, bh + off, idesc, 1u);
+            mma_bf16(d, ah + off, bl + off, idesc, 1u);
+            mma_bf16(d, am + off, bm + off, idesc, 1u);
+            mma_bf16(d, al + off, bh + off, idesc, 1u);
+          }
+          mma_commit(bars + 64 + 8 * s);  // stage free once these MMAs have read it
         }
-        mma_commit(bars + 64 + 8 * s);  // stage free once these MMAs have read it
+        if (ok) mma_commit(bars + 128 + 8 * b);  // accumulator half b complete
       }
-      mma_commit(bars + 128);           // accumulator complete
+      mma_commit(bars + 192);
+      mbar_wait(bars + 192, 0u, status);  // every MMA of this CTA has completed
     }
   } else {
     // epilogue warps 2..5: lane quadrant (warp % 4) of the accumulator
     const int quad = warp & 3;
-    const bool ok = mbar_wait(bars + 128, 0u, status);
-    tc_fence_after();
-    const int row = m0 + quad * 32 + lane;
+    int tl = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
+      const int b = tl & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(bars + 128 + 8 * b, (uint32_t)(tl >> 1) & 1u, status));
+      tc_fence_after();
+      const int row = (t % mtiles) * TC_BM + quad * 32 + lane;
+      const int n0 = (t / mtiles) * TC_BN;
 #pragma unroll 1
-    for (int c = 0; c < TC_BN / 16; ++c) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 16), v);
-      if (!ok || row >= m_valid) continue;
+      for (int c = 0; c < TC_BN / 16; ++c) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TC_BN + c * 16), v);
+        if (!ok || row >= m_valid) continue;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int col = n0 + c * 16 + j;
-        if (col < ncols) C[(long long)(col_base + col) * ldc + row] = v[j];
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c * 16 + j;
+          if (col < ncols) C[(long long)(col_base + col) * ldc + row] = v[j];
+        }
       }
+      tc_fence_before();
+      mbar_arrive(bars + 160 + 8 * b);
+      if (!ok) break;
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TC_BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * TC_BN))
+                 : "memory");
   }
 }
 
@@ -372,10 +405,18 @@ int tc_prepare_operators(TcPlan* p, const double2* W, const double2* T, double w
 
 static int launch_tc_gemm(TcPlan* p, int which_A, const CUtensorMap* b, int col_base, int ncols, float* C,
                           cudaStream_t s) {
-  dim3 grid(p->Mp / TC_BM, (ncols + TC_BN - 1) / TC_BN);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+    cudaGetLastError();
+  }
+  const int mtiles = p->Mp / TC_BM, ntiles = (ncols + TC_BN - 1) / TC_BN;
+  const int grid = std::min(mtiles * ntiles, sms);
   k_tc_gemm<<<grid, 192, SMEM_BYTES, s>>>(p->mA_hi[which_A], p->mA_mid[which_A], p->mA_lo[which_A], b[0], b[1], b[2],
-                                          p->Kp / TC_BK, col_base, ncols,
-                                          2 * p->N, C, 2LL * p->N, p->status);
+                                          p->Kp / TC_BK, col_base, ncols, 2 * p->N, mtiles, ntiles, C, 2LL * p->N,
+                                          p->status);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
