@@ -72,7 +72,7 @@ typedef struct {
   double penal;         /* chi = rho^penal (>= 1); density and compliance are linear in chi */
   int nbands;           /* lowest bands returned per k, 1..24, and nbands <= 3N/3 */
   int precision;        /* PC_FP64 | PC_MIXED */
-  double tol;           /* relative residual target of the block iteration (0: default) */
+  double tol;           /* relative residual target of the block iteration (0: default, 1e-8 FP64, 3e-4 mixed) */
   int max_iter;         /* iteration cap (0: default); hitting it sets PC_ENOCONV */
 } pc_params;
 
