@@ -52,6 +52,10 @@ int best_split(int units, int len, int max_parts) {
   return best;
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // (re, im) bf16 pair -> (im, -re): swap the halves, then flip the sign of the upper half.
 __device__ __forceinline__ uint32_t rot_pair(uint32_t w) { return __funnelshift_l(w, w, 16) ^ 0x80000000u; }
 
@@ -141,6 +145,8 @@ __global__ __launch_bounds__(G_THREADS, 1) void k_tc_gram(TcGramArgs a) {
         const int r = r0 + qq[u];
         x0[u] = r < r_end ? colp[u][r] : make_float2(0.f, 0.f);
         x1[u] = r + 1 < r_end ? colp[u][r + 1] : make_float2(0.f, 0.f);
+        // stage it + 2 into L2 (no registers held), so its loads one stage later hit there
+        if (r + 64 < r_end) prefetch_l2(colp[u] + r + 64);
       }
     };
     auto stash = [&](int it, const float2 (&x0)[G_MAXI], const float2 (&x1)[G_MAXI]) {
@@ -381,6 +387,19 @@ __global__ __launch_bounds__(U_THREADS, 1) void k_tc_update(TcUpdateArgs a) {
         if (ip_u[u] < nip && r < a.n3) {
           if (i0 < ncols) x0[u] = colp[i0][r];
           if (i0 + 1 < ncols) x1[u] = colp[i0 + 1][r];
+        }
+      }
+      // stage it + 2 into L2 (no registers held), so its loads one stage later hit there
+      const int it2 = it + 2;
+      if (it2 < nstage) {
+        const int tl2 = it2 / nat, at2 = it2 % nat;
+        const int r02 = (tile0 + tl2) * 128;
+        const int nip2 = min(64, ((Kt - 64 * at2 + 15) / 16) * 16) / 4;
+#pragma unroll
+        for (int u = 0; u < U_MAXI; ++u) {
+          const int r = r02 + rr_u[u];
+          const int i0 = 32 * at2 + 2 * ip_u[u];
+          if (ip_u[u] < nip2 && r < a.n3 && i0 < ncols) prefetch_l2(colp[i0] + r);
         }
       }
     };
