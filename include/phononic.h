@@ -204,8 +204,12 @@ int pc_apply_operator(pc_ctx* ctx, int k, int ncols, const double* x_dev,
  * rows, nk problems) and what = 1 the basis update out = [S] C with two coefficient sets,
  * three operand triplets and an identity last block (nblk > 1), once on the split-BF16
  * tensor cores and once on the FP32 CUDA cores; *rel_err = max |difference| / max |CUDA-core
- * result|.  Not on the hot path.  Errors: PC_EINVAL (m > 24, nblk > 3, bad what or sizes),
- * PC_ENOMEM, PC_ECUDA, PC_ETIMEOUT (a bounded wait of a tensor-core kernel expired). */
+ * result|.  what = 2 exercises the failure path of the kernels' bounded barrier waits: a
+ * one-thread kernel waits on a barrier that nothing completes, with a short limit; *rel_err = 0
+ * when it gave up and recorded PC_ETIMEOUT and the device then accepted further work, else 1
+ * (the other arguments are ignored).  Not on the hot path.  Errors: PC_EINVAL (m > 24,
+ * nblk > 3, bad what or sizes), PC_ENOMEM, PC_ECUDA, PC_ETIMEOUT (a bounded wait of a
+ * tensor-core kernel expired during what = 0 or 1). */
 int pc_check_tensor_kernels(int what, int nk, int m, int nblk, int n3, double* rel_err);
 
 /* --- Allocation-free entry point (no counterpart in the paper) ---

@@ -591,6 +591,19 @@ int launch_update_tc(const UpdateArgs<float>& u, int* status, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Self-check of the tensor-core kernels against the CUDA-core kernels on seeded data.
 namespace {
+// A wait that cannot complete: no thread arrives on the barrier, so the bounded wait used by
+// every tensor-core kernel must give up after `limit` polls, record PC_ETIMEOUT and return.
+__global__ void k_wait_expiry(int* status, long long limit) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(b, 0u, status, limit);
+}
+
 __global__ void k_fill_hash(float2* p, long long n, unsigned long long seed, int n3) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -620,8 +633,24 @@ double max_abs_diff(const float2* a, const float2* b, long long n, double* ref_m
 }  // namespace
 
 extern "C" int pc_check_tensor_kernels(int what, int nk, int m, int nblk, int n3, double* rel_err) {
-  if (!rel_err || nk < 1 || m < 1 || m > 24 || nblk < 1 || nblk > 3 || n3 < 1 || (what != 0 && what != 1))
-    return PC_EINVAL;
+  if (!rel_err) return PC_EINVAL;
+  if (what == 2) {  // failure path of the bounded waits
+    *rel_err = -1.0;
+    int* st = nullptr;
+    if (cudaMalloc(&st, sizeof(int)) != cudaSuccess) return PC_ENOMEM;
+    int h = -1;
+    bool ok = cudaMemset(st, 0, sizeof(int)) == cudaSuccess;
+    k_wait_expiry<<<1, 32>>>(st, 1 << 14);
+    ok = ok && cudaDeviceSynchronize() == cudaSuccess;
+    ok = ok && cudaMemcpy(&h, st, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    // the context must still take work after the expired wait
+    ok = ok && cudaMemset(st, 0, sizeof(int)) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+    cudaFree(st);
+    if (!ok) { cudaGetLastError(); return PC_ECUDA; }
+    *rel_err = (h == PC_ETIMEOUT) ? 0.0 : 1.0;
+    return PC_OK;
+  }
+  if (nk < 1 || m < 1 || m > 24 || nblk < 1 || nblk > 3 || n3 < 1 || (what != 0 && what != 1)) return PC_EINVAL;
   *rel_err = -1.0;
   const long long blk = (long long)nk * m * n3;
   float2 *in = nullptr, *out_tc = nullptr, *out_ref = nullptr, *C = nullptr, *part = nullptr;

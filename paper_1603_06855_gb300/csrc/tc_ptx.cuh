@@ -32,8 +32,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait; false (and PC_ETIMEOUT recorded) when the limit expires.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
-  for (long long i = 0; i < WAIT_LIMIT; ++i)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, long long limit = WAIT_LIMIT) {
+  for (long long i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   atomicCAS(status, 0, PC_ETIMEOUT);
   return false;

@@ -38,3 +38,12 @@ def test_gram_tensor_cores(B, nk, m, nblk, n3):
 def test_update_tensor_cores(B, nk, m, nblk, n3):
     err = B.pc_check_tensor_kernels(1, nk, m, nblk, n3)
     assert 0 <= err < TOL, err
+
+
+def test_bounded_wait_expires(B):
+    """Failure detection without a fault: a kernel waits on a barrier that nothing completes,
+    with a short poll limit.  It must give up, record PC_ETIMEOUT in its status word and
+    return, and the device must accept further work; the tensor-core kernels then still agree
+    with the CUDA-core ones."""
+    assert B.pc_check_tensor_kernels(2, 1, 1, 1, 1) == 0.0
+    assert 0 <= B.pc_check_tensor_kernels(0, 2, 8, 1, 64) < TOL
