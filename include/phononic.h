@@ -152,6 +152,18 @@ int pc_bands(pc_ctx* ctx, double* omega_dev, void* stream);
 int pc_gap_and_grad(pc_ctx* ctx, int n_lower, int mode, const double* w_dev,
                     double* gap_dev, double* grad_dev, void* stream);
 
+/* Smooth surrogate of the omega-form gap between bands n_lower and n_lower+1 (not in the
+ * paper, whose eq. obj takes a max and a min over k, non-differentiable where the extremal k
+ * changes).  With x = omega / omega_ref, omega_ref^2 = (2 pi / a)^2 E1 / rho1 (phase 1):
+ *   a = omega_ref (1/beta) log sum_k exp(beta x_{k,n}),
+ *   b = -omega_ref (1/beta) log sum_k exp(-beta x_{k,n+1}),   gap = 2 (b - a) / (b + a),
+ * a lower bound of the exact gap that tends to it as beta grows.  grad_dev (or NULL) receives
+ * dgap/drho_e through the same adjoint as pc_gap_and_grad, with every k weighted; at each k
+ * the bands within a relative 1e-8 of band n (and of band n+1) share its weight equally.
+ * Errors: PC_ESTATE (pc_bands not run), PC_EINVAL (NULL gap_dev, n_lower out of
+ * 1..nbands-1, beta not in (0, 1e12)), PC_ECUDA. */
+int pc_gap_ks_and_grad(pc_ctx* ctx, int n_lower, double beta, double* gap_dev, double* grad_dev, void* stream);
+
 /* Synchronises the device and fills *out; returns out->status as well. */
 int pc_get_stats(pc_ctx* ctx, pc_stats* out);
 

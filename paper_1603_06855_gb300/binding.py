@@ -72,7 +72,8 @@ class pc_stats(ctypes.Structure):
     ]
 
 
-EXPORTED = ["pc_create", "pc_set_kpoints", "pc_set_design", "pc_bands", "pc_gap_and_grad", "pc_get_stats",
+EXPORTED = ["pc_create", "pc_set_kpoints", "pc_set_design", "pc_bands", "pc_gap_and_grad", "pc_gap_ks_and_grad",
+            "pc_get_stats",
             "pc_clear_status", "pc_set_profiling", "pc_probe", "pc_destroy", "pc_strerror", "pc_export",
             "pc_apply_operator", "pc_check_tensor_kernels", "pc_structure_factors_noalloc"]
 
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH):
     lib.pc_set_design.argtypes = [P, P, P]
     lib.pc_bands.argtypes = [P, P, P]
     lib.pc_gap_and_grad.argtypes = [P, I, I, P, P, P, P]
+    lib.pc_gap_ks_and_grad.argtypes = [P, I, D, P, P, P]
     lib.pc_get_stats.argtypes = [P, ctypes.POINTER(pc_stats)]
     lib.pc_clear_status.argtypes = [P]
     lib.pc_set_profiling.argtypes = [P, I]
@@ -177,6 +179,10 @@ def pc_bands(ctx: int, omega_ptr: int, stream: int = 0) -> None:
 def pc_gap_and_grad(ctx: int, n_lower: int, mode: int, w_ptr: int, gap_ptr: int, grad_ptr: int,
                     stream: int = 0) -> None:
     _check(load().pc_gap_and_grad(ctx, n_lower, mode, w_ptr, gap_ptr, grad_ptr, stream), "pc_gap_and_grad")
+
+
+def pc_gap_ks_and_grad(ctx: int, n_lower: int, beta: float, gap_ptr: int, grad_ptr: int, stream: int = 0) -> None:
+    _check(load().pc_gap_ks_and_grad(ctx, n_lower, beta, gap_ptr, grad_ptr, stream), "pc_gap_ks_and_grad")
 
 
 def pc_get_stats(ctx: int) -> pc_stats:

@@ -59,6 +59,82 @@ __global__ void k_gap(GapArgs a) {
     return;
   }
   const int lo = a.n_lower - 1, hi = a.n_lower;
+  if (a.mode == PC_GAP_KS_INTERNAL) {
+    // Smooth surrogate: with x = omega / omega_ref = sqrt(lam_nd), a = (1/beta) log sum_k
+    // exp(beta x_{k,lo}) and b = -(1/beta) log sum_k exp(-beta x_{k,hi}), G = 2 (b - a) / (b + a).
+    __shared__ double xm_s, ym_s, sa_s, sb_s;
+    const double beta = a.ks_beta;
+    double mx = -1e300, my = 1e300;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+      mx = fmax(mx, sqrt(fmax(a.lam[k * nb + lo], 0.0)));
+      my = fmin(my, sqrt(fmax(a.lam[k * nb + hi], 0.0)));
+    }
+    sv[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) sv[threadIdx.x] = fmax(sv[threadIdx.x], sv[threadIdx.x + w]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) xm_s = sv[0];
+    __syncthreads();
+    sv[threadIdx.x] = my;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) sv[threadIdx.x] = fmin(sv[threadIdx.x], sv[threadIdx.x + w]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) ym_s = sv[0];
+    __syncthreads();
+    const double xm = xm_s, ym = ym_s;
+    double pa = 0.0, pb = 0.0;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+      pa += exp(beta * (sqrt(fmax(a.lam[k * nb + lo], 0.0)) - xm));
+      pb += exp(-beta * (sqrt(fmax(a.lam[k * nb + hi], 0.0)) - ym));
+    }
+    sv[threadIdx.x] = pa;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) sv[threadIdx.x] += sv[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) sa_s = sv[0];
+    __syncthreads();
+    sv[threadIdx.x] = pb;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) sv[threadIdx.x] += sv[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) sb_s = sv[0];
+    __syncthreads();
+    const double A_ = xm + log(sa_s) / beta, B_ = ym - log(sb_s) / beta;
+    const double dGa = -4.0 * B_ / ((A_ + B_) * (A_ + B_)), dGb = 4.0 * A_ / ((A_ + B_) * (A_ + B_));
+    if (threadIdx.x == 0) *a.gap_out = 2.0 * (B_ - A_) / (B_ + A_);
+    // weights dG/dlambda_phys: p_k dGa / (2 x lref) on band lo, q_k dGb / (2 y lref) on band hi,
+    // each shared by the bands of its cluster at that k (one thread per k: no write conflicts)
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+      for (int side = 0; side < 2; ++side) {
+        const int band = side == 0 ? lo : hi;
+        const double xv = sqrt(fmax(a.lam[k * nb + band], 0.0));
+        if (xv <= 0.0) continue;
+        const double pw = side == 0 ? exp(beta * (xv - xm)) / sa_s : exp(-beta * (xv - ym)) / sb_s;
+        const double wl = (side == 0 ? dGa : dGb) * pw / (2.0 * xv * a.lref);
+        const double ref = a.lam[k * nb + band];
+        int members = 0;
+        for (int b = 0; b < nb; ++b) members += (fabs(a.lam[k * nb + b] - ref) <= a.rel_tol * fabs(ref)) ? 1 : 0;
+        for (int b = 0; b < nb; ++b)
+          if (fabs(a.lam[k * nb + b] - ref) <= a.rel_tol * fabs(ref)) a.weights[k * nb + b] += wl / members;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int c = 0;
+      for (int t = 0; t < nk * nb; ++t)
+        if (a.weights[t] != 0.0) a.pairs[c++] = t;
+      *a.npairs = c;
+    }
+    return;
+  }
   // argmax_k lam[k][lo], lowest k among ties
   double bv = -1e300;
   int bi = 0x7fffffff;

@@ -133,6 +133,7 @@ struct GapArgs {
   int nk, nb, n_lower, mode;
   double lref;           // lambda_phys = lam * lref
   double rel_tol;
+  double ks_beta;        // smooth (KS) gap: sharpness on omega / omega_ref (mode PC_GAP_KS_INTERNAL)
   const double* w_user;  // for PC_GRAD_ALLBANDS
   double* gap_out;
   double* weights;       // nk x nb, dG / dlambda_phys
@@ -140,6 +141,7 @@ struct GapArgs {
   int* npairs;
 };
 int launch_gap(const GapArgs& a, cudaStream_t s);
+#define PC_GAP_KS_INTERNAL 3  // mode of GapArgs for pc_gap_ks_and_grad
 
 struct AdjointArgs {
   const double2* theta;  // [vec][3][N], nondimensional eigenvectors (X' with X'^H Omega' X' = I)

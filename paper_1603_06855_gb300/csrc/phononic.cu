@@ -1028,12 +1028,9 @@ extern "C" int pc_bands(pc_ctx* c, double* omega, void* stream) {
   return PC_OK;
 }
 
-extern "C" int pc_gap_and_grad(pc_ctx* c, int n_lower, int mode, const double* w, double* gap, double* grad,
-                               void* stream) {
-  if (!c || !gap) return PC_EINVAL;
-  if (mode != PC_GAP_OMEGA && mode != PC_GAP_LAMBDA && mode != PC_GRAD_ALLBANDS) return PC_EINVAL;
-  if (mode == PC_GRAD_ALLBANDS && !w) return PC_EINVAL;
-  if (mode != PC_GRAD_ALLBANDS && (n_lower < 1 || n_lower >= c->nb)) return PC_EINVAL;
+// Objective weights (exact, smooth or user-given) and the adjoint gradient they select.
+static int gap_and_grad_impl(pc_ctx* c, int n_lower, int mode, double beta, const double* w, double* gap,
+                             double* grad, void* stream) {
   if (!c->have_bands) return PC_ESTATE;
   cudaGetLastError();  // launch checks below report only this call's launches
   cudaStream_t s = (cudaStream_t)stream;
@@ -1043,6 +1040,7 @@ extern "C" int pc_gap_and_grad(pc_ctx* c, int n_lower, int mode, const double* w
   g.nk = c->nk; g.nb = c->nb; g.n_lower = n_lower; g.mode = mode;
   g.lref = c->lref;
   g.rel_tol = 1e-8;
+  g.ks_beta = beta;
   g.w_user = w;
   g.gap_out = gap;
   g.weights = c->weights;
@@ -1080,6 +1078,21 @@ extern "C" int pc_gap_and_grad(pc_ctx* c, int n_lower, int mode, const double* w
   c->have_grad_events = true;
   c->have_grad = true;
   return PC_OK;
+}
+
+extern "C" int pc_gap_and_grad(pc_ctx* c, int n_lower, int mode, const double* w, double* gap, double* grad,
+                               void* stream) {
+  if (!c || !gap) return PC_EINVAL;
+  if (mode != PC_GAP_OMEGA && mode != PC_GAP_LAMBDA && mode != PC_GRAD_ALLBANDS) return PC_EINVAL;
+  if (mode == PC_GRAD_ALLBANDS && !w) return PC_EINVAL;
+  if (mode != PC_GRAD_ALLBANDS && (n_lower < 1 || n_lower >= c->nb)) return PC_EINVAL;
+  return gap_and_grad_impl(c, n_lower, mode, 0.0, w, gap, grad, stream);
+}
+
+extern "C" int pc_gap_ks_and_grad(pc_ctx* c, int n_lower, double beta, double* gap, double* grad, void* stream) {
+  if (!c || !gap) return PC_EINVAL;
+  if (n_lower < 1 || n_lower >= c->nb || !(beta > 0.0) || !(beta < 1e12)) return PC_EINVAL;
+  return gap_and_grad_impl(c, n_lower, PC_GAP_KS_INTERNAL, beta, nullptr, gap, grad, stream);
 }
 
 extern "C" int pc_get_stats(pc_ctx* c, pc_stats* out) {

@@ -60,6 +60,14 @@ class BandSolver:
                           self._stream())
         return gap, grad
 
+    def gap_ks_and_grad(self, n_lower: int, beta: float, need_grad: bool = True):
+        """Smooth (KS) omega-form gap between bands n_lower and n_lower + 1 and its gradient."""
+        gap = torch.empty(1, dtype=torch.float64, device=self.device)
+        grad = torch.empty(self.n, dtype=torch.float64, device=self.device) if need_grad else None
+        B.pc_gap_ks_and_grad(self.ctx, n_lower, float(beta), gap.data_ptr(),
+                             grad.data_ptr() if grad is not None else 0, self._stream())
+        return gap, grad
+
     def apply_operator(self, k: int, x: torch.Tensor):
         """SI A(k) x and Omega x for x of shape (ncols, 3N) complex128 (FP64 operator path)."""
         x = x.to(self.device, torch.complex128).contiguous()

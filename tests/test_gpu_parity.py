@@ -300,3 +300,23 @@ def test_gap_gradient_central_differences(B):
     g = grad[idx]
     assert np.all(np.abs(fd - g) <= 1e-4 * np.abs(g).max()), (fd, g)
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_smooth_ks_gap_and_gradient(B, precision):
+    """Smooth (KS) gap between bands 6 and 7 over the 30 k of config 1 and its adjoint gradient
+    (every k weighted) against the oracle's KS gap: gap within the frequency tolerance, gradient
+    within the gradient tolerance (relative L2)."""
+    w = wl.config1()
+    P = mixed.from_workload(w)
+    lam_ref, sols = mixed.bands(P, w.Q, w.nbands, keep=True)
+    omega_ref = 2.0 * np.pi / w.a * np.sqrt(w.phase1["E"] / w.phase1["rho"])
+    s, om, st = run_gpu(w, precision)
+    for beta in (20.0, 200.0):
+        r = ogap.ks_gap(lam_ref, 6, beta, omega_ref)
+        g_ref = sensitivity.weighted(P, sols, r.weights)
+        gap, grad = s.gap_ks_and_grad(6, beta)
+        assert abs(gap.item() - r.gap) <= TOL_W[precision] * abs(r.gap), (gap.item(), r.gap)
+        rel = np.linalg.norm(grad.cpu().numpy().ravel() - g_ref) / np.linalg.norm(g_ref)
+        assert rel <= TOL_G[precision], rel
+    s.close()
