@@ -219,7 +219,9 @@ int pc_apply_operator(pc_ctx* ctx, int k, int ncols, const double* x_dev,
  * result|.  what = 2 exercises the failure path of the kernels' bounded barrier waits: a
  * one-thread kernel waits on a barrier that nothing completes, with a short limit; *rel_err = 0
  * when it gave up and recorded PC_ETIMEOUT and the device then accepted further work, else 1
- * (the other arguments are ignored).  Not on the hot path.  Errors: PC_EINVAL (m > 24,
+ * (the other arguments are ignored).  Not on the hot path; it switches the library's Gram and
+ * update kernel path for its own launches, so it must not run concurrently with other calls.
+ * Errors: PC_EINVAL (m > 24,
  * nblk > 3, bad what or sizes), PC_ENOMEM, PC_ECUDA, PC_ETIMEOUT (a bounded wait of a
  * tensor-core kernel expired during what = 0 or 1). */
 int pc_check_tensor_kernels(int what, int nk, int m, int nblk, int n3, double* rel_err);
