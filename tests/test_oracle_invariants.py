@@ -93,6 +93,26 @@ def test_fcc_primitive_permutation_and_inversion():
     assert np.allclose(base, inv, rtol=1e-11)
 
 
+def test_bcc_primitive_point_group():
+    """BCC primitive cell a1 = (-1,1,1)/2, a2 = (1,-1,1)/2, a3 = (1,1,-1)/2: the Cartesian
+    x <-> y reflection swaps a1 and a2, the cyclic permutation x -> y -> z cycles a1, a2, a3,
+    and inversion maps s -> -s.  Each, applied to the design's fractional axes and to Q
+    together, leaves the bands unchanged; the design permuted alone does not."""
+    rng = np.random.default_rng(19)
+    rho = rng.uniform(0, 1, (5, 5, 5))
+    Q = np.array([0.17, 0.29, 0.06])
+
+    def lam(r, q):
+        return mixed.bands(_problem("bcc", r.shape, 1, r), [q], 8)[0]
+
+    base = lam(rho, Q)
+    assert np.allclose(base, lam(np.transpose(rho, (1, 0, 2)), Q[[1, 0, 2]]), rtol=1e-11)
+    assert np.allclose(base, lam(np.transpose(rho, (1, 2, 0)), Q[[1, 2, 0]]), rtol=1e-11)
+    assert np.allclose(base, lam(rho[::-1, ::-1, ::-1], -Q), rtol=1e-11)
+    moved = lam(np.transpose(rho, (1, 2, 0)), Q)
+    assert np.max(np.abs(moved - base) / base[-1]) > 1e-6
+
+
 def test_element_sum_is_k_independent():
     """The element-sum matrices do not depend on the wavevector (Q cancels in K_q - K_p)."""
     rng = np.random.default_rng(18)
