@@ -101,6 +101,29 @@ def test_gap_matches_paper_band_edges():
         assert abs(g_lambda - c["printed_gap_pct"]) > 10.0
 
 
+def test_sphere_inclusion_gaps_match_paper():
+    """Tungsten-carbide spheres in epoxy with the paper's constants, one per primitive cell, at
+    the volume fractions where the paper's scans peak: gap(6,7) lies within 3 percentage points
+    of the printed maxima at M = 3, the cutoff of the paper's optimization runs.  The pin is
+    approximate because the paper states neither the cutoff nor the grid of these scans, and
+    the cutoff alone moves the BCC and FCC gaps by 3-5 points between M = 3 and M = 4.  Other
+    constants (the stiffer WC of the benchmark workloads) or a 20 % heavier inclusion move the
+    gap by 2-7 points; swapping the phases closes it.  Only the distinct high-symmetry points
+    are sampled: for these designs the gap edges sit there (within 0.1 point of a 31-point
+    boundary path)."""
+    cases = json.load(open(os.path.join(GOLDEN, "paper_sphere_inclusions.json")))["cases"]
+    n = (24, 24, 24)
+    got = {}
+    for c in cases:
+        rho = wl.sphere_inclusion(c["lattice"], n, c["volume_fraction"])
+        assert abs(rho.mean() - c["volume_fraction"]) < 2e-3
+        P = mixed.build(c["lattice"], n, 3, rho, wl.PAPER_WC, wl.PAPER_EPOXY, 1.0)
+        lam = mixed.bands(P, wl.high_symmetry_points(c["lattice"]), 8)
+        got[c["lattice"]] = gap.gap(lam, 6).gap * 100
+        assert abs(got[c["lattice"]] - c["printed_gap_pct"]) <= 3.0, (c, got)
+    assert min(got["bcc"], got["fcc"]) > got["sc"] + 20.0
+
+
 def test_gap_weights_are_the_gradient_of_the_gap():
     rng = np.random.default_rng(5)
     lam = np.sort(rng.uniform(1.0, 9.0, size=(7, 5)), axis=1)

@@ -236,3 +236,33 @@ def laminate(n1: int, n_other: int, M: int, frac1: float, kx: list[float]) -> Wo
 
 def random_design(n, rng, low=0.05, high=0.95) -> np.ndarray:
     return rng.uniform(low, high, size=tuple(n))
+
+
+def high_symmetry_points(lattice: str) -> np.ndarray:
+    """The distinct high-symmetry points of the irreducible zone, reduced coordinates (n, 3)."""
+    A = _primitive(lattice)
+    return np.array([np.array(p, float) @ A for p in HIGH_SYMMETRY[lattice].values()])
+
+
+def sphere_inclusion(lattice: str, n, vf: float, sub: int = 3) -> np.ndarray:
+    """One sphere per primitive cell, centred on the lattice points, of volume fraction vf.
+
+    rho_e is the share of the voxel inside the sphere, estimated on sub^3 points per voxel
+    (the voxel's own cell of a sub x sub x sub grid); the distance to the nearest lattice
+    point uses the 27 neighbouring cells, which covers every point of the cell for these
+    primitive vectors.  A = cubic lattice constant 1."""
+    A = _primitive(lattice)
+    V = abs(np.linalg.det(A))
+    r = (3.0 * vf * V / (4.0 * math.pi)) ** (1.0 / 3.0)
+    n = tuple(int(v) for v in n)
+    idx = np.indices(n).reshape(3, -1).T.astype(float)
+    o = (np.arange(sub) + 0.5) / sub
+    shifts = np.array([(i, j, l) for i in (-1, 0, 1) for j in (-1, 0, 1) for l in (-1, 0, 1)], float)
+    inside = np.zeros(idx.shape[0])
+    for d in np.array([(a, b, c) for a in o for b in o for c in o]):
+        s = (idx + d) / np.array(n, float)
+        dist = np.full(s.shape[0], np.inf)
+        for sh in shifts:
+            dist = np.minimum(dist, np.linalg.norm((s - sh) @ A.T, axis=1))
+        inside += dist <= r
+    return (inside / sub ** 3).reshape(n)
