@@ -31,6 +31,7 @@ import workloads as wl  # noqa: E402
 
 METRIC = "design·k band+adjoint solves/s (FCC, N=729, 20 bands) mixed vs FP64; % roofline"
 UNIT = "(design*k)/s"
+BENCH_WORKLOAD = "fcc32_M4_levelset"
 WORKLOAD = "fcc32_M4_levelset: FCC primitive cell, 32^3 voxels, N=729 plane waves, 100 k, 20 bands"
 
 
@@ -44,13 +45,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--cpu-k", type=int, default=2, help="k-points in the oracle sample")
-    ap.add_argument("--config", type=int, default=3, choices=[1, 2, 3],
-                    help="workload; 3 is the benchmark, 1-2 are smaller cases for profiler captures")
+    ap.add_argument("--workload", default=BENCH_WORKLOAD,
+                    choices=["sc16_M2_grf", "bcc24_M3_grf", BENCH_WORKLOAD],
+                    help="the FCC N = 729 workload is the benchmark; the others are smaller cases "
+                         "for profiler captures")
     return ap.parse_args()
 
 
-def designs(count: int, rank: int, config: int = 3):
-    gen = {1: wl.config1, 2: wl.config2, 3: wl.config3}[config]
+def designs(count: int, rank: int, workload: str = BENCH_WORKLOAD):
+    gen = wl.WORKLOADS[workload]
     return [gen(design=rank * 1000 + i) for i in range(count)]
 
 
@@ -133,11 +136,11 @@ class ClockSampler:
 
 
 def cpu_baseline(nk_sample: int):
-    """The FP64 oracle (as it stands) on one config-3 design: per-design assembly and
+    """The FP64 oracle (as it stands) on one FCC N = 729 design: per-design assembly and
     Phi^-1 once, then nk_sample wavevectors with their all-band adjoint.  The per
     (design . k) time is extrapolated to the 100-k design: (t_design + 100 t_k) / 100."""
     from oracle import mixed, sensitivity
-    w = wl.config3(design=0)
+    w = wl.fcc32_levelset(design=0)
     t0 = time.perf_counter()
     P = mixed.from_workload(w)
     P.phi_inv()
@@ -217,7 +220,7 @@ def main():
             dist.barrier()
 
     nsteps = args.warmup + args.steps
-    ws = designs(min(nsteps, 4), rank, args.config)
+    ws = designs(min(nsteps, 4), rank, args.workload)
     w0 = ws[0]
     rhos = [torch.from_numpy(w.rho.ravel()).to(dev) for w in ws]
     wts = torch.from_numpy(all_band_weights(w0)).to(dev)
@@ -372,7 +375,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 block iteration (split-bf16x3 tensor-core contractions, f32 projected problems) + f64 Rayleigh-Ritz",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.config == 3 else ws[0].name, "designs_per_step": 1, "k_per_design": w0.nk, "bands": w0.nbands,
+            "config": {"workload": WORKLOAD if args.workload == BENCH_WORKLOAD else ws[0].name, "designs_per_step": 1, "k_per_design": w0.nk, "bands": w0.nbands,
                        "adjoint": "all-band weighted (every (k, band))",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "clocks": ck,
@@ -395,7 +398,7 @@ def main():
             "roofline_families": fam,
             "fp64_form": fp64,
             "peaks_measured": {"fp64_tflops": fp64_peak / 1e3, "fp32_tflops": fp32_peak / 1e3}}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == 3:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == BENCH_WORKLOAD:
         line["cpu_baseline"] = cpu_baseline(args.cpu_k)
     if rank == 0:
         print(json.dumps(line), flush=True)

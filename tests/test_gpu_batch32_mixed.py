@@ -45,8 +45,8 @@ def _err(got, ref):
     return np.max(np.abs(got - ref) / np.maximum(ref, 0.05 * ref.max()))
 
 
-def test_config4_uneven_batch(B):
-    designs = wl.config4()
+def test_uneven_batch32(B):
+    designs = wl.batch32_mixed()
     seen = set()
     worst = {}
     for w in designs:

@@ -35,7 +35,7 @@ def B():
 
 def test_fcc729_bench_workload_sampled_k(B):
     from paper_1603_06855_gb300.solver import BandSolver
-    w = wl.config3()
+    w = wl.fcc32_levelset()
     P = mixed.from_workload(w)
     lam_ref, sols = mixed.bands(P, w.Q[SAMPLE], w.nbands, keep=True)
 

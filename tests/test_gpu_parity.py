@@ -69,11 +69,11 @@ def run_gpu(w, precision, Q=None, **kw):
 
 
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("cfg", [0, 1])
-def test_assembly_matches_element_sums(B, cfg):
+@pytest.mark.parametrize("name", ["sc8_M1_binary_cube", "sc16_M2_grf"])
+def test_assembly_matches_element_sums(B, name):
     """Structure factors -> Toeplitz operators (eqs. loop, matrixofintegral, intOmega, intPhi)
     and the inverse compliance operators, against the oracle's element sums."""
-    w = wl.CONFIGS[cfg]()
+    w = wl.WORKLOADS[name]()
     P = mixed.from_workload(w)
     s = solver_for(w, "fp64")
     s.set_design(torch.from_numpy(w.rho.ravel()).cuda())
@@ -91,15 +91,16 @@ def test_assembly_matches_element_sums(B, cfg):
     s.close()
 
 
-@pytest.mark.parametrize("cfg,ks", [(0, [0, 3, 9]), (1, [0, 11]), (2, [5])])
-def test_operator_apply_matches_dense(B, cfg, ks):
+@pytest.mark.parametrize("name,ks,seed", [("sc8_M1_binary_cube", [0, 3, 9], 31), ("sc16_M2_grf", [0, 11], 32),
+                                          ("bcc24_M3_grf", [5], 33)])
+def test_operator_apply_matches_dense(B, name, ks, seed):
     """A(k) x = H Phi^-1 H^* x and Omega x (eq. matrixform) for seeded random x, several
     columns that span more than one GEMM tile."""
-    w = wl.CONFIGS[cfg]()
+    w = wl.WORKLOADS[name]()
     P = mixed.from_workload(w)
     s = solver_for(w, "fp64")
     s.set_design(torch.from_numpy(w.rho.ravel()).cuda())
-    rng = np.random.default_rng(31 + cfg)
+    rng = np.random.default_rng(seed)
     n3 = 3 * P.N
     ncols = 70
     for k in ks:
@@ -113,16 +114,17 @@ def test_operator_apply_matches_dense(B, cfg, ks):
     s.close()
 
 
-@pytest.mark.parametrize("cfg,ks", [(0, [0, 4]), (1, [3, 20]), (2, [7])])
-def test_mixed_operator_apply(B, cfg, ks):
+@pytest.mark.parametrize("name,ks,seed", [("sc8_M1_binary_cube", [0, 4], 71), ("sc16_M2_grf", [3, 20], 72),
+                                          ("bcc24_M3_grf", [7], 73)])
+def test_mixed_operator_apply(B, name, ks, seed):
     """The mixed form's operator (FP32 vectors, split-BF16 tensor-core products accumulated in
     FP32) against the dense FP64 operator: relative Frobenius error <= 2e-5 per block and
     max-entry error <= 1e-4 of the largest entry."""
-    w = wl.CONFIGS[cfg]()
+    w = wl.WORKLOADS[name]()
     P = mixed.from_workload(w)
     s = solver_for(w, "mixed")
     s.set_design(torch.from_numpy(w.rho.ravel()).cuda())
-    rng = np.random.default_rng(71 + cfg)
+    rng = np.random.default_rng(seed)
     n3 = 3 * P.N
     ncols = min(300, w.nk * s.stats().block)  # block width: bands + guard vectors
     for k in ks:
@@ -140,9 +142,9 @@ def test_mixed_operator_apply(B, cfg, ks):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("cfg", [0, 1])
-def test_bands_match_oracle(B, cfg, precision):
-    w = wl.CONFIGS[cfg]()
+@pytest.mark.parametrize("name", ["sc8_M1_binary_cube", "sc16_M2_grf"])
+def test_bands_match_oracle(B, name, precision):
+    w = wl.WORKLOADS[name]()
     P = mixed.from_workload(w)
     lam_ref = mixed.bands(P, w.Q, w.nbands)
     s, om, st = run_gpu(w, precision)
@@ -159,8 +161,8 @@ def test_bands_match_oracle(B, cfg, precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_gap_and_gradient_match_oracle(B, precision):
-    """Config 1: gap(3,4) and gap(6,7) in the omega form and the full 4096-element gradient."""
-    w = wl.config1()
+    """SC 16^3 random field (M = 2, 30 k): gap(3,4) and gap(6,7) in the omega form and the full 4096-element gradient."""
+    w = wl.sc16_grf()
     P = mixed.from_workload(w)
     lam_ref, sols = mixed.bands(P, w.Q, w.nbands, keep=True)
     s, om, st = run_gpu(w, precision)
@@ -183,7 +185,7 @@ def test_gap_and_gradient_match_oracle(B, precision):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_weighted_all_bands_gradient(B, precision):
     """PC_GRAD_ALLBANDS: seeded weights on every (k, band) except the Gamma zero modes."""
-    w = wl.config0()
+    w = wl.sc8_binary_cube()
     rng = np.random.default_rng(41)
     rho = np.clip(0.15 + 0.7 * w.rho + 0.05 * rng.standard_normal(w.rho.shape), 0, 1)
     w.rho = rho
@@ -203,9 +205,9 @@ def test_weighted_all_bands_gradient(B, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_config2_sampled_k(B, precision):
+def test_bcc24_sampled_k(B, precision):
     """BCC 24^3, N = 343: bands and gap(6,7) gradient on a sample of the 64 k-points."""
-    w = wl.config2()
+    w = wl.bcc24_grf()
     idx = [0, 9, 31, 63]
     Q = w.Q[idx]
     P = mixed.from_workload(w)
@@ -240,7 +242,7 @@ def test_edge_cases(B):
     assert omega_err(om, ref) <= 1e-9
     s.close()
     # out-of-range density
-    w = wl.config0()
+    w = wl.sc8_binary_cube()
     s = solver_for(w, "fp64")
     bad = w.rho.ravel().copy()
     bad[5] = 1.5
@@ -252,7 +254,7 @@ def test_edge_cases(B):
 
 def test_autograd_function(B):
     from paper_1603_06855_gb300.solver import BandSolver, gap
-    w = wl.config0()
+    w = wl.sc8_binary_cube()
     rng = np.random.default_rng(61)
     rho0 = np.clip(0.1 + 0.8 * w.rho + 0.05 * rng.standard_normal(w.rho.shape), 0, 1)
     s = BandSolver.from_workload(w)
@@ -275,7 +277,7 @@ def test_gap_gradient_central_differences(B):
     largest sensitivities and two random ones; agreement within 1e-4 relative (truncation
     O(h^2) and the 1e-8 residual target keep the difference quotient to ~1e-7)."""
     from paper_1603_06855_gb300.solver import BandSolver
-    w = wl.config1()
+    w = wl.sc16_grf()
     s = BandSolver.from_workload(w)
     rho = torch.from_numpy(w.rho.ravel()).cuda()
     s.set_design(rho)
@@ -304,10 +306,10 @@ def test_gap_gradient_central_differences(B):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_smooth_ks_gap_and_gradient(B, precision):
-    """Smooth (KS) gap between bands 6 and 7 over the 30 k of config 1 and its adjoint gradient
+    """Smooth (KS) gap between bands 6 and 7 over the 30 k of the SC 16^3 random-field workload and its adjoint gradient
     (every k weighted) against the oracle's KS gap: gap within the frequency tolerance, gradient
     within the gradient tolerance (relative L2)."""
-    w = wl.config1()
+    w = wl.sc16_grf()
     P = mixed.from_workload(w)
     lam_ref, sols = mixed.bands(P, w.Q, w.nbands, keep=True)
     omega_ref = 2.0 * np.pi / w.a * np.sqrt(w.phase1["E"] / w.phase1["rho"])

@@ -51,10 +51,10 @@ def _gap_and_grad(w, rho, n_lower, ks=None):
     return r, sensitivity.weighted(P, sols, r.weights)
 
 
-def test_gap_gradient_fd_config0():
+def test_gap_gradient_fd_sc8_cube():
     """Whole-objective gradient vs central differences on the 8^3 SC cell (p = 1), binary cube
     perturbed by seeded noise so that no degeneracy sits on the extremal bands."""
-    w = wl.config0()
+    w = wl.sc8_binary_cube()
     rng = np.random.default_rng(23)
     rho = np.clip(0.1 + 0.8 * w.rho + 0.05 * rng.standard_normal(w.rho.shape), 0.0, 1.0)
     r, g = _gap_and_grad(w, rho, 3)
@@ -70,15 +70,15 @@ def test_gap_gradient_fd_config0():
 
 
 @pytest.mark.slow
-def test_gap_gradient_fd_config1():
-    """Config 1 (SC 16^3, p = 3, GRF): gap(6,7) gradient vs central differences, step 1e-6, on
+def test_gap_gradient_fd_sc16_grf():
+    """SC 16^3 random field (p = 3): gap(6,7) gradient vs central differences, step 1e-6, on
     20 seeded elements.  The difference quotient re-solves only the two extremal wavevectors,
     which stay extremal under a 1e-6 perturbation."""
-    w = wl.config1()
+    w = wl.sc16_grf()
     rho = w.rho
     r, g = _gap_and_grad(w, rho, 6)
     ks = [r.k_lower, r.k_upper]
-    rng = np.random.default_rng(wl.seed_for(1))
+    rng = np.random.default_rng(w.seed)
     h = 1e-6
     errs = []
     for e in rng.choice(rho.size, 20, replace=False):
@@ -120,7 +120,7 @@ def test_inversion_maps_gradient():
 def test_cluster_sum_is_basis_independent():
     """A degenerate pair at a high-symmetry point: the summed sensitivity is unchanged by a
     unitary rotation inside the pair."""
-    w = wl.config0()
+    w = wl.sc8_binary_cube()
     P = mixed.from_workload(w)
     Q = w.Q[-1]  # R point of the symmetric cube inclusion
     sol = mixed.solve_k(P, Q, 6)

@@ -29,7 +29,7 @@ def _worker(rank: int, world: int, port: int, out_dir: str) -> None:
     import torch.distributed as dist
     import bench
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    ds = bench.designs(2, rank, config=1)
+    ds = bench.designs(2, rank, workload="sc16_M2_grf")
     seeds = [d.seed for d in ds]
     gathered = [None] * world
     dist.all_gather_object(gathered, seeds)
@@ -53,8 +53,8 @@ def test_two_gloo_ranks(tmp_path):
     assert ms == 180.0                       # the slowest rank
     sys.path.insert(0, ROOT)
     import workloads as wl
-    nk = wl.config1().nk
+    nk = wl.sc16_grf().nk
     assert value == pytest.approx(world * nk / 0.180)
     seeds = r0[2:].astype(int)
     assert len(set(seeds.tolist())) == len(seeds)  # disjoint designs across ranks
-    assert seeds.tolist() == [wl.config1(design=r * 1000 + i).seed for r in range(world) for i in range(2)]
+    assert seeds.tolist() == [wl.sc16_grf(design=r * 1000 + i).seed for r in range(world) for i in range(2)]

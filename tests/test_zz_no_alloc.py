@@ -35,7 +35,7 @@ def _regular(B, w, rho):
 
 def test_noalloc_matches_regular_path_twice(B):
     """Two calls in a row (different designs and sizes) against pc_set_design's structure factors."""
-    cases = [wl.config1(), wl.config0()]
+    cases = [wl.sc16_grf(), wl.sc8_binary_cube()]
     cases[1].rho = np.clip(0.2 + 0.6 * cases[1].rho + 0.05 * np.random.default_rng(3).standard_normal(cases[1].n), 0, 1)
     stream = torch.cuda.current_stream().cuda_stream
     for w in cases:
@@ -51,7 +51,7 @@ def test_noalloc_matches_regular_path_twice(B):
 
 
 def test_noalloc_rejects_oversized_grids(B):
-    w = wl.config1()
+    w = wl.sc16_grf()
     p = B.make_params(w.lattice, (48, 48, 48), w.M, w.nbands, w.phase1, w.phase0, w.penal)
     rho = torch.zeros(48 ** 3, dtype=torch.float64, device="cuda")
     out = torch.zeros(3 * (4 * w.M + 1) ** 3 * 2, dtype=torch.float64, device="cuda")

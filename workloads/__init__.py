@@ -1,6 +1,6 @@
 """Seeded synthetic inputs shared by the oracle tests, the CUDA parity tests and the bench.
 
-This module holds only input preparation: material constants, the five workload
+This module holds only input preparation: material constants, the workload
 configurations, seeded density designs and Bloch wavevector paths.  It contains
 none of the band-structure or sensitivity arithmetic, and it imports neither the
 oracle nor the CUDA binding.
@@ -10,15 +10,16 @@ designs with the same shapes stand in for them):
 
 * two-phase tungsten-carbide / epoxy cells on SC, BCC and FCC primitive cells,
   voxel densities rho_e in [0, 1] with rho_e = 1 the stiff, heavy phase;
-* config 0: SC 8^3 binary cube inclusion, M = 1, 10 k on G-X-M-G-R, 6 bands;
-* config 1: SC 16^3 periodic Gaussian random field through a sigmoid, p = 3,
+* sc8_M1_binary_cube: SC 8^3 binary cube inclusion, M = 1, 10 k on G-X-M-G-R, 6 bands;
+* sc16_M2_grf: SC 16^3 periodic Gaussian random field through a sigmoid, p = 3,
   M = 2, 30 k on the irreducible-zone boundary, 12 bands;
-* config 2: BCC 24^3 random field in fractional coordinates, M = 3, 64 k, 16 bands;
-* config 3: FCC 32^3 smoothed level set of an 8-term trigonometric sum,
+* bcc24_M3_grf: BCC 24^3 random field in fractional coordinates, M = 3, 64 k, 16 bands;
+* fcc32_M4_levelset: FCC 32^3 smoothed level set of an 8-term trigonometric sum,
   M = 4 (729 plane waves), 100 k, 20 bands;
-* config 4: 32 designs of mixed lattice, cutoff and grid, 48 k, 20 bands.
+* batch32_mixed: 32 designs of mixed lattice, cutoff and grid, 48 k, 20 bands;
+* sphere_inclusion: one sphere per primitive cell, as in the paper's volume-fraction scans.
 
-Seeds: numpy.random.default_rng(1603 + 1000 * config + design_index).
+Seeds: numpy.random.default_rng(SEED_BASE[workload] + design_index).
 """
 from __future__ import annotations
 
@@ -163,48 +164,52 @@ class Workload:
         return self.Q.shape[0]
 
 
-def seed_for(config: int, design: int = 0) -> int:
-    return 1603 + 1000 * config + design
+SEED_BASE = {"sc8_M1_binary_cube": 1603, "sc16_M2_grf": 2603, "bcc24_M3_grf": 3603,
+             "fcc32_M4_levelset": 4603, "batch32_mixed": 5603}
 
 
-def config0() -> Workload:
+def _seed(workload: str, design: int = 0) -> int:
+    return SEED_BASE[workload] + design
+
+
+def sc8_binary_cube() -> Workload:
     n = (8, 8, 8)
     rho = np.zeros(n)
     rho[2:6, 2:6, 2:6] = 1.0
     return Workload("sc8_M1_binary_cube", "sc", n, 1, 6, kpath("sc", 10, "sc_short"), rho,
-                    1.0, (3,), seed_for(0))
+                    1.0, (3,), _seed("sc8_M1_binary_cube"))
 
 
-def config1(design: int = 0) -> Workload:
-    seed = seed_for(1, design)
+def sc16_grf(design: int = 0) -> Workload:
+    seed = _seed("sc16_M2_grf", design)
     rng = np.random.default_rng(seed)
     n = (16, 16, 16)
     z = gaussian_random_field(n, 1.0 / 6.0, rng, cart=np.eye(3))
     return Workload("sc16_M2_grf", "sc", n, 2, 12, kpath("sc", 30), _sigmoid(z), 3.0, (3, 6), seed)
 
 
-def config2(design: int = 0) -> Workload:
-    seed = seed_for(2, design)
+def bcc24_grf(design: int = 0) -> Workload:
+    seed = _seed("bcc24_M3_grf", design)
     rng = np.random.default_rng(seed)
     n = (24, 24, 24)
     z = gaussian_random_field(n, 1.0 / 6.0, rng)
     return Workload("bcc24_M3_grf", "bcc", n, 3, 16, kpath("bcc", 64), _sigmoid(z), 3.0, (6,), seed)
 
 
-def config3(design: int = 0) -> Workload:
-    seed = seed_for(3, design)
+def fcc32_levelset(design: int = 0) -> Workload:
+    seed = _seed("fcc32_M4_levelset", design)
     rng = np.random.default_rng(seed)
     n = (32, 32, 32)
     rho = trig_levelset_design(n, rng)
     return Workload("fcc32_M4_levelset", "fcc", n, 4, 20, kpath("fcc", 100), rho, 3.0, (6,), seed)
 
 
-def config4() -> list[Workload]:
+def batch32_mixed() -> list[Workload]:
     """Uneven batch: 12 SC, 10 BCC, 10 FCC designs; N drawn from {125, 343, 729, 1331}."""
     out = []
     lattices = ["sc"] * 12 + ["bcc"] * 10 + ["fcc"] * 10
     for i, lat in enumerate(lattices):
-        seed = seed_for(4, i)
+        seed = _seed("batch32_mixed", i)
         rng = np.random.default_rng(seed)
         M = int(rng.choice([2, 3, 4, 5]))
         grid_choices = [g for g in (16, 20, 24, 28, 32, 36, 40) if g >= 2 * M + 1]
@@ -217,7 +222,8 @@ def config4() -> list[Workload]:
     return out
 
 
-CONFIGS = {0: config0, 1: config1, 2: config2, 3: config3}
+WORKLOADS = {"sc8_M1_binary_cube": sc8_binary_cube, "sc16_M2_grf": sc16_grf,
+             "bcc24_M3_grf": bcc24_grf, "fcc32_M4_levelset": fcc32_levelset}
 
 
 def homogeneous(lattice: str, n, M: int, nbands: int, nk: int, value: float = 0.0) -> Workload:
