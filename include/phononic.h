@@ -44,6 +44,9 @@ extern "C" {
 #define PC_BCC  1
 #define PC_FCC  2
 
+/* Largest wavevector count of one context (pc_set_kpoints). */
+#define PC_MAX_KPOINTS 65535
+
 /* Arithmetic of the eigensolver. */
 #define PC_FP64   0  /* every step in FP64 on CUDA cores */
 #define PC_MIXED  1  /* split-BF16 tensor-core operator, FP32 block iteration,
@@ -120,8 +123,9 @@ int pc_create(const pc_params* params, pc_ctx** out);
 /* Sets the Bloch wavevectors: q_reduced_host holds nk rows of (Q1, Q2, Q3), the
  * reduced coordinates of the paper's K = T1 (Q1 + alpha) + T2 (Q2 + beta) + T3 (Q3 + gamma)
  * (reciprocal basis without 2 pi).  Allocates the block-iteration workspaces for nk
- * points (synchronous; not for use inside stream capture).
- * Errors: PC_EINVAL (nk < 1 or NULL), PC_ENOMEM. */
+ * points (synchronous; not for use inside stream capture).  nk is at most
+ * PC_MAX_KPOINTS per context; larger sets are split over several contexts.
+ * Errors: PC_EINVAL (NULL, nk < 1 or nk > PC_MAX_KPOINTS), PC_ENOMEM. */
 int pc_set_kpoints(pc_ctx* ctx, const double* q_reduced_host, int nk);
 
 /* Sets the design: rho_dev holds n0*n1*n2 FP64 densities in [0, 1], C order.

@@ -407,7 +407,8 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
 }
 
 extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
-  if (!c || !q || nk < 1 || nk > 100000) return PC_EINVAL;
+  // The wavevector index is a grid dimension (y) of several launches: at most 65535.
+  if (!c || !q || nk < 1 || nk > PC_MAX_KPOINTS) return PC_EINVAL;
   free_kset(c);
   const int m = c->m, N = c->N, n3 = 3 * N;
   const size_t nvec = (size_t)nk * m;

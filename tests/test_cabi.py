@@ -60,3 +60,18 @@ def test_null_handles_rejected():
     assert lib.pc_gap_and_grad(None, 1, 0, None, None, None, None) == B.PC_EINVAL
     assert lib.pc_clear_status(None) == B.PC_EINVAL
     lib.pc_destroy(None)
+
+
+def test_kpoint_count_limit():
+    """nk outside [1, PC_MAX_KPOINTS] (the wavevector index is a launch grid dimension) is
+    rejected before the context is used: the placeholder handle is never dereferenced."""
+    import ctypes
+    B = _lib()
+    lib = B.load()
+    hdr = open(os.path.join(ROOT, "include", "phononic.h")).read()
+    limit = int(re.search(r"#define PC_MAX_KPOINTS\s+(\d+)", hdr).group(1))
+    assert limit == 65535
+    q = ctypes.create_string_buffer(24 * (limit + 1))
+    placeholder = ctypes.create_string_buffer(64)
+    for nk in (0, -1, limit + 1):
+        assert lib.pc_set_kpoints(ctypes.addressof(placeholder), ctypes.addressof(q), nk) == B.PC_EINVAL
