@@ -151,8 +151,15 @@ int pc_bands(pc_ctx* ctx, double* omega_dev, void* stream);
  * 1e-8 of the extremal one at that k share its weight equally.  For PC_GRAD_ALLBANDS,
  * w_dev holds nk*nbands weights, n_lower is ignored, gap_dev receives sum w*lambda
  * and grad_dev sum_{k,b} w[k,b] dlambda_{k,b}/drho_e.
+ * The gradient stages, per CTA, the N coefficients of one field component and the
+ * voxel phase tables in shared memory: N + (2M+1)^2 n2 + (2M+1)(n1 + n2) complex values
+ * (16 bytes in the FP64 form, 8 in the mixed form) must fit in 200 KiB.  For cubic grids
+ * n^3 that is n <= 197 / 121 / 80 (FP64) and n <= 256 / 251 / 169 (mixed) at M = 3 / 4 / 5,
+ * any n <= 256 at M <= 2; larger grids get PC_EINVAL when grad_dev is given (bands and the
+ * gap alone have no such limit).
  * Errors: PC_ESTATE (pc_bands not run), PC_EINVAL (n_lower out of 1..nbands-1,
- * bad mode, NULL w_dev for PC_GRAD_ALLBANDS), PC_ECUDA. */
+ * bad mode, NULL w_dev for PC_GRAD_ALLBANDS, the grid limit above; all detected before
+ * anything is enqueued), PC_ECUDA. */
 int pc_gap_and_grad(pc_ctx* ctx, int n_lower, int mode, const double* w_dev,
                     double* gap_dev, double* grad_dev, void* stream);
 
@@ -165,7 +172,8 @@ int pc_gap_and_grad(pc_ctx* ctx, int n_lower, int mode, const double* w_dev,
  * dgap/drho_e through the same adjoint as pc_gap_and_grad, with every k weighted; at each k
  * the bands within a relative 1e-8 of band n (and of band n+1) share its weight equally.
  * Errors: PC_ESTATE (pc_bands not run), PC_EINVAL (NULL gap_dev, n_lower out of
- * 1..nbands-1, beta not in (0, 1e12)), PC_ECUDA. */
+ * 1..nbands-1, beta not in (0, 1e12), the gradient's grid limit of pc_gap_and_grad),
+ * PC_ECUDA. */
 int pc_gap_ks_and_grad(pc_ctx* ctx, int n_lower, double beta, double* gap_dev, double* grad_dev, void* stream);
 
 /* Synchronises the device and fills *out; returns out->status as well. */

@@ -295,18 +295,23 @@ __global__ void k_adj_reduce(AdjointArgs a) {
   a.grad[e] = acc * a.inv_sO * a.ve * a.dchi[e];
 }
 
+size_t adjoint_staging_bytes(int M, int n1, int n2, bool fp32) {
+  const size_t M2 = 2 * (size_t)M + 1;
+  const size_t elems = M2 * M2 * M2 + M2 * M2 * (size_t)n2 + M2 * (size_t)n2 + M2 * (size_t)n1;
+  return elems * (fp32 ? sizeof(float2) : sizeof(double2));
+}
+
 template <typename R>
 static int launch_adjoint_t(const AdjointArgs& a, cudaStream_t s) {
-  typedef typename cplx_t<R>::type C2;
   const int M2 = 2 * a.M + 1;
   if (M2 > 11) return PC_EINVAL;
-  size_t sm = sizeof(C2) * ((size_t)a.N + (size_t)M2 * M2 * a.n2 + (size_t)M2 * a.n2 + (size_t)M2 * a.n1);
+  const size_t sm = adjoint_staging_bytes(a.M, a.n1, a.n2, sizeof(R) == sizeof(float));
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_adj_synth12<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_adj_synth12<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjointStagingMax);
     attr = true;
   }
-  if (sm > 200 * 1024) return PC_EINVAL;
+  if (sm > kAdjointStagingMax) return PC_EINVAL;
   dim3 g1(a.max_pairs, 9);
   k_adj_synth12<R><<<g1, 256, sm, s>>>(a);
   PC_LAUNCH_CHECK();

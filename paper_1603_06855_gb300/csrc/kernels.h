@@ -163,6 +163,11 @@ struct AdjointArgs {
 };
 // fp32: synthesis in FP32 (mixed form); the weighted sum is accumulated in FP64 either way.
 int launch_adjoint(const AdjointArgs& a, bool fp32, cudaStream_t s);
+// Dynamic shared memory of the adjoint's field-synthesis kernel: the N coefficients of one
+// eigenvector component plus the (2M+1)^2 n2 and (2M+1)(n1 + n2) phase tables, complex values
+// of the form's precision.  Grids and cutoffs above kAdjointStagingMax are refused.
+size_t adjoint_staging_bytes(int M, int n1, int n2, bool fp32);
+constexpr size_t kAdjointStagingMax = 200 * 1024;
 
 // omega[k][b] = sqrt(max(lam_m[k][b] * lref, 0)) and lam_nd[k][b] = lam_m[k][b] for b < nb.
 int launch_omega(const double* lam_m, int nk, int nb, int m, double lref, double* omega, double* lam_nd,

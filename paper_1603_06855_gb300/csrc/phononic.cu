@@ -1033,6 +1033,10 @@ extern "C" int pc_bands(pc_ctx* c, double* omega, void* stream) {
 static int gap_and_grad_impl(pc_ctx* c, int n_lower, int mode, double beta, const double* w, double* gap,
                              double* grad, void* stream) {
   if (!c->have_bands) return PC_ESTATE;
+  // Refused before anything is enqueued: the adjoint's shared staging must fit.
+  if (grad && adjoint_staging_bytes(c->prm.M, c->prm.n[1], c->prm.n[2], c->prm.precision == PC_MIXED) >
+                  kAdjointStagingMax)
+    return PC_EINVAL;
   cudaGetLastError();  // launch checks below report only this call's launches
   cudaStream_t s = (cudaStream_t)stream;
   PC_CUDA_TRY(cudaEventRecord(c->ev_g0, s));
