@@ -306,11 +306,11 @@ static int launch_adjoint_t(const AdjointArgs& a, cudaStream_t s) {
   const int M2 = 2 * a.M + 1;
   if (M2 > 11) return PC_EINVAL;
   const size_t sm = adjoint_staging_bytes(a.M, a.n1, a.n2, sizeof(R) == sizeof(float));
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_adj_synth12<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjointStagingMax);
-    attr = true;
-  }
+  // Set once per instantiation; a function-local static is initialised exactly once even when
+  // k groups on several host threads arrive together.
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_adj_synth12<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjointStagingMax);
+  (void)attr;
   if (sm > kAdjointStagingMax) return PC_EINVAL;
   dim3 g1(a.max_pairs, 9);
   k_adj_synth12<R><<<g1, 256, sm, s>>>(a);

@@ -405,13 +405,13 @@ int tc_prepare_operators(TcPlan* p, const double2* W, const double2* T, double w
 
 static int launch_tc_gemm(TcPlan* p, int which_A, const CUtensorMap* b, int col_base, int ncols, float* C,
                           cudaStream_t s) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  static const int sms = [] {  // queried once; thread-safe static initialisation
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
     cudaGetLastError();
-  }
+    return v;
+  }();
   const int mtiles = p->Mp / TC_BM, ntiles = (ncols + TC_BN - 1) / TC_BN;
   const int grid = std::min(mtiles * ntiles, sms);
   k_tc_gemm<<<grid, 192, SMEM_BYTES, s>>>(p->mA_hi[which_A], p->mA_mid[which_A], p->mA_lo[which_A], b[0], b[1], b[2],

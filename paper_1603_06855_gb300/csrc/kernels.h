@@ -101,7 +101,9 @@ template <typename R> struct UpdateArgs {
 };
 template <typename R> int launch_update(const UpdateArgs<R>& a, cudaStream_t s);
 // Tensor-core versions for FP32 data (tall_tc.cu); g_tc_tall = 0 selects the CUDA-core kernels.
-extern int g_tc_tall;
+// Process-wide switches read by every launch, from any k-group thread.
+extern std::atomic<int> g_tc_tall;
+extern std::atomic<int> g_acc64;  // lobpcg.cu: FP64 accumulation in the FP32 Gram/update (experiments)
 int launch_gram_tc(const float2* const A[3], int na, const float2* const B[3], int nbk, int nk, int m, int n3,
                    float scale, float2* part, int max_split, float2* G, int* status, cudaStream_t s);
 int launch_update_tc(const UpdateArgs<float>& u, int* status, cudaStream_t s);

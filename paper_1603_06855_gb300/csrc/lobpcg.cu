@@ -13,7 +13,7 @@
 #define GRAM_SPLIT 8
 #define GRAM_LD 73   // odd row stride of the shared tiles (columns up to 72)
 
-int g_acc64 = 0;  // experiment switch: FP64 accumulation in the FP32 Gram and update kernels
+std::atomic<int> g_acc64{0};  // experiment switch: FP64 accumulation in the FP32 Gram and update kernels
 
 // G_part[k][split] = A^H B over one row range; each of the 16 x 16 threads holds TILE x TILE outputs.  Shared tiles are double-buffered: the next
 // tile of GRAM_ROWS rows (16 in FP32, 8 in FP64: 37 KB of static shared memory either way)
@@ -634,11 +634,10 @@ int launch_small_rr(const typename cplx_t<R>::type* GA, const typename cplx_t<R>
                     R drop_tol, const int* kdone, R* lam_out, typename cplx_t<R>::type* coef, int* status,
                     cudaStream_t s) {
   size_t sm = SmallSmem<R>::bytes(n);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_small_rr<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  // Once per instantiation (thread-safe static initialisation: k groups run on several host threads).
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_small_rr<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  (void)attr;
   if (sm > 200 * 1024) return PC_EINVAL;
   k_small_rr<R><<<nk, SMALL_THREADS, sm, s>>>(GA, GO, n, m, drop_tol, kdone, lam_out, coef, status);
   PC_LAUNCH_CHECK();
@@ -806,11 +805,9 @@ int launch_small_pdir(const typename cplx_t<R>::type* GO, const typename cplx_t<
   typedef typename cplx_t<R>::type C2;
   if (m > 24 || n > 72) return PC_EINVAL;
   size_t sm = sizeof(C2) * (3 * (size_t)n * m + (size_t)m * m + m) + sizeof(R) * m + sizeof(int) * m + 64;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_small_pdir<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  static const cudaError_t attr =  // once per instantiation, thread-safe
+      cudaFuncSetAttribute(k_small_pdir<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  (void)attr;
   k_small_pdir<R><<<nk, 256, sm, s>>>(GO, CX, n, m, kdone, abs_drop, CP);
   PC_LAUNCH_CHECK();
   return PC_OK;

@@ -22,7 +22,6 @@
 #include "kernels.h"
 #include "gemm_tc.h"
 
-extern int g_acc64;     // lobpcg.cu: FP64 accumulation switch (experiments)
 
 std::atomic<long long> g_pc_launches{0};
 

@@ -21,20 +21,20 @@
 
 using namespace tcx;
 
-int g_tc_tall = 1;  // tensor-core Gram and update kernels for FP32 data (0: CUDA cores)
+std::atomic<int> g_tc_tall{1};  // tensor-core Gram and update kernels for FP32 data (0: CUDA cores)
 
 namespace {
 
 constexpr int A_SLICE = 128 * 128;  // 128 rows x 64 bf16 (one 128-byte swizzle atom along K)
 
 int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
+  static const int n = [] {  // queried once; thread-safe static initialisation
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
     cudaGetLastError();
-  }
+    return v;
+  }();
   return n;
 }
 
@@ -507,11 +507,10 @@ __global__ __launch_bounds__(U_THREADS, 1) void k_tc_update(TcUpdateArgs a) {
 
 template <int MOUT, int NC>
 void set_update_smem() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(k_tc_update<MOUT, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM);
-    done = true;
-  }
+  // Once per instantiation; static initialisation is thread-safe (k groups run on several host threads).
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_tc_update<MOUT, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM);
+  (void)attr;
 }
 
 }  // namespace
@@ -522,13 +521,11 @@ int launch_gram_reduce_f(const float2* part, int nsplit, int nel, int nk, float 
 int launch_gram_tc(const float2* const A[3], int na, const float2* const B[3], int nbk, int nk, int m, int n3,
                    float scale, float2* part, int max_split, float2* G, int* status, cudaStream_t s) {
   if (na * m > 72 || nbk * m > 72 || nk < 1) return PC_EINVAL;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM) != cudaSuccess) {
-      cudaGetLastError();
-      return PC_ECUDA;
-    }
-    attr = true;
+  static const cudaError_t attr =  // once, thread-safe static initialisation
+      cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM);
+  if (attr != cudaSuccess) {
+    cudaGetLastError();
+    return PC_ECUDA;
   }
   const int S = (n3 + 31) / 32;
   int ns = best_split(nk, S, max_split);
