@@ -87,6 +87,30 @@ def test_laminate_converges_to_rytov():
     assert errs[2] < 2e-2
 
 
+def test_laminate_optimum_matches_paper():
+    """The paper's 1-D optimum (first gap of a WC/epoxy bilayer, maximal at WC fraction 0.737)
+    from the exact Rytov relation at the zone boundary k d = pi, gap in the omega form through
+    the oracle's gap function.  Waves of speed sqrt(E/rho) (rod) and shear waves both give the
+    printed value within 0.4 points and peak within 0.005 of the printed fraction; pressure waves
+    peak at 154.5 % near 0.724, so the printed scan is not of pressure waves."""
+    c = json.load(open(os.path.join(GOLDEN, "paper_laminate_optimum.json")))
+    p1, p0 = wl.PAPER_WC, wl.PAPER_EPOXY
+    (cL1, cT1), (cL0, cT0) = _speeds(p1), _speeds(p0)
+    rod1, rod0 = np.sqrt(p1["E"] / p1["rho"]), np.sqrt(p0["E"] / p0["rho"])
+
+    def first_gap(f, c1, c0):
+        edges = _rytov_roots(np.pi, f, 1 - f, c1, c0, p1["rho"] * c1, p0["rho"] * c0, 2.0e5, 2)
+        return gap.gap((edges[None, :] ** 2), 1, gap.MODE_OMEGA).gap * 100
+
+    fs = np.arange(0.700, 0.7705, 0.005)
+    for c1, c0 in ((rod1, rod0), (cT1, cT0)):
+        assert abs(first_gap(c["volume_fraction"], c1, c0) - c["printed_gap_pct"]) <= 0.4
+        g = [first_gap(f, c1, c0) for f in fs]
+        assert abs(fs[int(np.argmax(g))] - c["volume_fraction"]) <= 0.005 + 1e-9
+    gp = [first_gap(f, cL1, cL0) for f in fs]
+    assert abs(max(gp) - c["printed_gap_pct"]) > 0.8
+
+
 def test_gap_matches_paper_band_edges():
     """The omega form of the gap reproduces the percentages printed with the paper's band edges."""
     cases = json.load(open(os.path.join(GOLDEN, "paper_band_edges.json")))["cases"]
