@@ -25,6 +25,7 @@ It is the plain dense definition of the method, written from the paper:
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms
 (homogeneous media, Rytov laminates), invariants (Gamma zero modes, time
 reversal, translation, point group, inversion), brute-force finite differences
-and the band edges the paper prints.
+and the numbers the paper prints (band edges of its optimized cells, sphere-inclusion
+gaps, the 1-D laminate optimum).
 """
 from . import lattice, mixed, gap, sensitivity  # noqa: F401
