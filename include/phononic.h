@@ -73,7 +73,7 @@ typedef struct {
   pc_material phase1;   /* the phase at rho_e = 1 */
   pc_material phase0;   /* the phase at rho_e = 0 */
   double penal;         /* chi = rho^penal (>= 1); density and compliance are linear in chi */
-  int nbands;           /* lowest bands returned per k, 1..24, and nbands <= 3N/3 */
+  int nbands;           /* lowest bands returned per k: 1..24 and at most N */
   int precision;        /* PC_FP64 | PC_MIXED */
   double tol;           /* relative residual target of the block iteration (0: default, 1e-8 FP64, 3e-4 mixed) */
   int max_iter;         /* iteration cap (0: default); hitting it sets PC_ENOCONV */
