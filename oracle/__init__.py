@@ -21,6 +21,8 @@ It is the plain dense definition of the method, written from the paper:
                      ``sensitivityew``, ``diffOmega``, ``diffPhi``) in two forms: the
                      literal per-element matrices (tiny cases) and the voxel quadratic
                      forms they reduce to.
+* ``mma``         -- one step of the method of moving asymptotes for the box-constrained
+                     design problem (Methods, eq. ``topopt``; the paper names no optimizer).
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms
 (homogeneous media, Rytov laminates), invariants (Gamma zero modes, time
@@ -28,4 +30,4 @@ reversal, translation, point group, inversion), brute-force finite differences
 and the numbers the paper prints (band edges of its optimized cells, sphere-inclusion
 gaps, the 1-D laminate optimum).
 """
-from . import lattice, mixed, gap, sensitivity  # noqa: F401
+from . import lattice, mixed, gap, sensitivity, mma  # noqa: F401
