@@ -176,6 +176,25 @@ int pc_gap_and_grad(pc_ctx* ctx, int n_lower, int mode, const double* w_dev,
  * PC_ECUDA. */
 int pc_gap_ks_and_grad(pc_ctx* ctx, int n_lower, double beta, double* gap_dev, double* grad_dev, void* stream);
 
+/* One design update of the optimization loop of Methods, eq. topopt (maximise the gap subject
+ * only to xmin <= x_e <= xmax; the paper names no optimizer): a step of Svanberg's method of
+ * moving asymptotes, which with bounds alone solves each variable's convex subproblem in
+ * closed form.  Needs no context.  All arrays are n doubles on the device, owned by the caller:
+ *   x_dev      in: the current design x^k (e.g. the densities); out: x^(k+1);
+ *   df_dev     in: d(objective)/dx at x^k, of the objective being maximised (e.g. grad_dev of
+ *              pc_gap_ks_and_grad);
+ *   xold1_dev, xold2_dev  in: x^(k-1), x^(k-2); out: x^k, x^(k-1);
+ *   low_dev, upp_dev      in: the asymptotes of the previous step; out: this step's.
+ * iter = k, the number of steps taken before this one: for iter < 2 the asymptotes start at
+ * x -/+ (xmax - xmin)/2 and the four history arrays are read but not used.  Later steps scale
+ * the asymptote distances by 0.7 where x oscillated and by 1.2 where it kept its direction,
+ * within [0.01, 10] (xmax - xmin) of x.  The new x stays within the bounds and within half the
+ * box of x^k.  Non-finite gradients give non-finite designs (not checked).
+ * Errors: PC_EINVAL (n < 1, a NULL array, iter < 0, xmin/xmax not finite or xmax <= xmin),
+ * PC_ECUDA. */
+int pc_mma_step(long long n, double* x_dev, const double* df_dev, double* xold1_dev, double* xold2_dev,
+                double* low_dev, double* upp_dev, int iter, double xmin, double xmax, void* stream);
+
 /* Synchronises the device and fills *out; returns out->status as well. */
 int pc_get_stats(pc_ctx* ctx, pc_stats* out);
 

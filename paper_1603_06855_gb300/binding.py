@@ -75,7 +75,7 @@ class pc_stats(ctypes.Structure):
 EXPORTED = ["pc_create", "pc_set_kpoints", "pc_set_design", "pc_bands", "pc_gap_and_grad", "pc_gap_ks_and_grad",
             "pc_get_stats",
             "pc_clear_status", "pc_set_profiling", "pc_probe", "pc_destroy", "pc_strerror", "pc_export",
-            "pc_apply_operator", "pc_check_tensor_kernels", "pc_structure_factors_noalloc"]
+            "pc_apply_operator", "pc_check_tensor_kernels", "pc_structure_factors_noalloc", "pc_mma_step"]
 
 _lib = None
 
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
     lib.pc_apply_operator.argtypes = [P, I, I, P, P, P, P]
     lib.pc_structure_factors_noalloc.argtypes = [ctypes.POINTER(pc_params), P, P, P]
     lib.pc_check_tensor_kernels.argtypes = [I, I, I, I, I, ctypes.POINTER(ctypes.c_double)]
+    lib.pc_mma_step.argtypes = [LL, P, P, P, P, P, P, I, D, D, P]
     for name in EXPORTED:
         if name not in ("pc_destroy", "pc_strerror"):
             getattr(lib, name).restype = I
@@ -183,6 +184,12 @@ def pc_gap_and_grad(ctx: int, n_lower: int, mode: int, w_ptr: int, gap_ptr: int,
 
 def pc_gap_ks_and_grad(ctx: int, n_lower: int, beta: float, gap_ptr: int, grad_ptr: int, stream: int = 0) -> None:
     _check(load().pc_gap_ks_and_grad(ctx, n_lower, beta, gap_ptr, grad_ptr, stream), "pc_gap_ks_and_grad")
+
+
+def pc_mma_step(n: int, x_ptr: int, df_ptr: int, xold1_ptr: int, xold2_ptr: int, low_ptr: int, upp_ptr: int,
+                iteration: int, xmin: float = 0.0, xmax: float = 1.0, stream: int = 0) -> None:
+    _check(load().pc_mma_step(n, x_ptr, df_ptr, xold1_ptr, xold2_ptr, low_ptr, upp_ptr, iteration, xmin, xmax,
+                              stream), "pc_mma_step")
 
 
 def pc_get_stats(ctx: int) -> pc_stats:

@@ -113,3 +113,48 @@ class GapFn(torch.autograd.Function):
 
 def gap(rho: torch.Tensor, solver: BandSolver, n_lower: int, mode: int = B.PC_GAP_OMEGA) -> torch.Tensor:
     return GapFn.apply(rho, solver, n_lower, mode)
+
+
+class MMA:
+    """Device state of the design update of eq. topopt (method of moving asymptotes with the
+    bounds as the only constraint) for n variables; each step is one pc_mma_step launch."""
+
+    def __init__(self, n: int, xmin: float = 0.0, xmax: float = 1.0, device="cuda"):
+        self.n = int(n)
+        self.xmin, self.xmax = float(xmin), float(xmax)
+        self.xold1, self.xold2, self.low, self.upp = (
+            torch.zeros(self.n, dtype=torch.float64, device=device) for _ in range(4))
+        self.device = self.xold1.device  # with its index ("cuda" -> "cuda:0"), as tensors report it
+        self.iteration = 0
+
+    def step(self, x: torch.Tensor, df: torch.Tensor) -> None:
+        """Moves x (contiguous float64 device tensor of n values) in place, ascending along df."""
+        if x.dtype != torch.float64 or not x.is_contiguous() or x.numel() != self.n or x.device != self.device:
+            raise ValueError("x must be a contiguous float64 tensor of n values on the solver's device")
+        df = df.detach().to(self.device, torch.float64).contiguous()
+        if df.numel() != self.n:
+            raise ValueError("gradient size does not match the design")
+        B.pc_mma_step(self.n, x.data_ptr(), df.data_ptr(), self.xold1.data_ptr(), self.xold2.data_ptr(),
+                      self.low.data_ptr(), self.upp.data_ptr(), self.iteration, self.xmin, self.xmax,
+                      torch.cuda.current_stream(self.device).cuda_stream)
+        self.iteration += 1
+
+
+def maximize_gap(solver: BandSolver, rho: torch.Tensor, n_lower: int, beta: float, steps: int):
+    """Optimization loop of eq. topopt on the smooth (KS) gap between bands n_lower and n_lower+1:
+    band structure, gap and adjoint gradient, then one MMA design update, `steps` times.  Returns
+    the final design (n0, n1, n2) and the gap before each step and after the last."""
+    x = rho.detach().to(solver.device, torch.float64).contiguous().clone().view(-1)
+    opt = MMA(x.numel(), device=solver.device)
+    history = []
+    for _ in range(steps):
+        solver.set_design(x)
+        solver.bands()
+        g, grad = solver.gap_ks_and_grad(n_lower, beta)
+        history.append(float(g.item()))
+        opt.step(x, grad.view(-1))
+    solver.set_design(x)
+    solver.bands()
+    g, _ = solver.gap_ks_and_grad(n_lower, beta, need_grad=False)
+    history.append(float(g.item()))
+    return x.view(solver.n), history

@@ -75,3 +75,24 @@ def test_kpoint_count_limit():
     placeholder = ctypes.create_string_buffer(64)
     for nk in (0, -1, limit + 1):
         assert lib.pc_set_kpoints(ctypes.addressof(placeholder), ctypes.addressof(q), nk) == B.PC_EINVAL
+
+
+def test_mma_step_rejects_bad_arguments():
+    """pc_mma_step validates its arguments on the host before launching anything; the
+    placeholder buffers below are never dereferenced."""
+    import ctypes
+    B = _lib()
+    lib = B.load()
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.addressof(buf)
+    good = dict(n=4, x=p, df=p, x1=p, x2=p, lo=p, up=p, it=0, xmin=0.0, xmax=1.0)
+
+    def call(**kw):
+        a = dict(good, **kw)
+        return lib.pc_mma_step(a["n"], a["x"], a["df"], a["x1"], a["x2"], a["lo"], a["up"], a["it"],
+                               a["xmin"], a["xmax"], None)
+
+    for bad in (dict(n=0), dict(n=-3), dict(x=None), dict(df=None), dict(x1=None), dict(x2=None),
+                dict(lo=None), dict(up=None), dict(it=-1), dict(xmax=0.0), dict(xmin=2.0),
+                dict(xmin=float("nan")), dict(xmax=float("inf"))):
+        assert call(**bad) == B.PC_EINVAL, bad
