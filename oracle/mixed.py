@@ -68,7 +68,7 @@ class Problem:
     rho_m: np.ndarray
     D: np.ndarray
     d_rho: float
-    d_D: np.ndarray
+    d_D: np.ndarray       # dD/dchi: (6, 6), or (ne, 6, 6) under the Young's-modulus law
     F: np.ndarray
     I: np.ndarray
     Omega: np.ndarray
@@ -91,16 +91,39 @@ class Problem:
         return self._phi_inv
 
 
-def material_fields(rho: np.ndarray, phase1: dict, phase0: dict, penal: float):
-    """chi = rho^p, dchi/drho, interpolated density and compliance per element."""
+def material_fields(rho: np.ndarray, phase1: dict, phase0: dict, penal: float, law: str = "compliance"):
+    """chi = rho^p, dchi/drho, interpolated density and compliance per element, and dD/dchi.
+
+    law "compliance": density and compliance linear in chi, so dD/dchi is the constant
+    difference of the phases (the element derivatives of eqs. diffOmega / diffPhi).
+    law "young": eq. combinematerial read literally, Young's modulus linear in chi (and
+    Poisson's ratio with it); each element has the compliance of its interpolated isotropic
+    material, D = (1/E) P1 + (nu/E) P2 with P1 = diag(1,1,1,2,2,2) and P2 = 2 on the shear
+    diagonal, -1 between normal components, so dD/dchi varies per element: (ne, 6, 6)."""
     r = np.asarray(rho, float).ravel()
     chi = r ** penal
     dchi = penal * r ** (penal - 1.0) if penal != 1.0 else np.ones_like(r)
-    D1 = compliance_voigt(phase1["E"], phase1["nu"])
-    D0 = compliance_voigt(phase0["E"], phase0["nu"])
     rho_m = phase0["rho"] + chi * (phase1["rho"] - phase0["rho"])
-    D = D0[None] + chi[:, None, None] * (D1 - D0)[None]
-    return chi, dchi, rho_m, D, phase1["rho"] - phase0["rho"], D1 - D0
+    if law == "compliance":
+        D1 = compliance_voigt(phase1["E"], phase1["nu"])
+        D0 = compliance_voigt(phase0["E"], phase0["nu"])
+        D = D0[None] + chi[:, None, None] * (D1 - D0)[None]
+        return chi, dchi, rho_m, D, phase1["rho"] - phase0["rho"], D1 - D0
+    if law != "young":
+        raise ValueError(law)
+    dE, dnu = phase1["E"] - phase0["E"], phase1["nu"] - phase0["nu"]
+    E = phase0["E"] + chi * dE
+    nu = phase0["nu"] + chi * dnu
+    D = np.stack([compliance_voigt(e, v) for e, v in zip(E, nu)])
+    P1 = np.diag([1.0, 1.0, 1.0, 2.0, 2.0, 2.0])
+    P2 = np.zeros((6, 6))
+    P2[:3, :3] = -1.0
+    P2[np.arange(3), np.arange(3)] = 0.0
+    P2[np.arange(3, 6), np.arange(3, 6)] = 2.0
+    da = -dE / E ** 2                      # d(1/E)/dchi
+    db = (dnu * E - nu * dE) / E ** 2      # d(nu/E)/dchi
+    d_D = da[:, None, None] * P1[None] + db[:, None, None] * P2[None]
+    return chi, dchi, rho_m, D, phase1["rho"] - phase0["rho"], d_D
 
 
 def element_sum(F: np.ndarray, w: np.ndarray) -> np.ndarray:
@@ -109,7 +132,7 @@ def element_sum(F: np.ndarray, w: np.ndarray) -> np.ndarray:
 
 
 def build(lattice: str, n, M: int, rho, phase1: dict, phase0: dict, penal: float = 1.0,
-          a: float = 1.0) -> Problem:
+          a: float = 1.0, law: str = "compliance") -> Problem:
     A = lat.primitive_vectors(lattice, a)
     T = lat.reciprocal_basis(A)
     V = lat.cell_volume(A)
@@ -118,7 +141,7 @@ def build(lattice: str, n, M: int, rho, phase1: dict, phase0: dict, penal: float
     x = s @ A.T
     ne = s.shape[0]
     ve = V / ne
-    chi, dchi, rho_m, D, d_rho, d_D = material_fields(rho, phase1, phase0, penal)
+    chi, dchi, rho_m, D, d_rho, d_D = material_fields(rho, phase1, phase0, penal, law)
     K0 = g @ T.T  # Q-independent part of K_q
     F = np.exp(1j * TWO_PI * (x @ K0.T))
     N = g.shape[0]

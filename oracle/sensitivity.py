@@ -34,7 +34,8 @@ def voxel(P: mixed.Problem, lam: float, theta: np.ndarray, s: np.ndarray) -> np.
     u = P.F @ theta.reshape(3, N).T        # (ne, 3) displacement at centroids
     sig = P.F @ s.reshape(6, N).T          # (ne, 6) Voigt stress at centroids
     mass = np.sum(np.abs(u) ** 2, axis=1)
-    comp = np.real(np.einsum("ev,vw,ew->e", sig.conj(), P.d_D, sig))
+    sub = "ev,vw,ew->e" if P.d_D.ndim == 2 else "ev,evw,ew->e"   # per-element dD/dchi (Young's-modulus law)
+    comp = np.real(np.einsum(sub, sig.conj(), P.d_D, sig))
     return P.dchi * P.ve * (-lam * P.d_rho * mass - comp)
 
 
@@ -50,7 +51,7 @@ def literal(P: mixed.Problem, Q, lam: float, theta: np.ndarray) -> np.ndarray:
     for e in range(P.F.shape[0]):
         f = np.outer(P.F[e].conj(), P.F[e]) * P.ve          # f^(e)_pq v^(e)
         dOm = P.dchi[e] * np.kron(np.eye(3), P.d_rho * f)
-        dPh = P.dchi[e] * np.kron(P.d_D, f)
+        dPh = P.dchi[e] * np.kron(P.d_D if P.d_D.ndim == 2 else P.d_D[e], f)
         term = (-Oinv @ dOm @ Oinv @ HPH - Oinv @ (H @ Phinv @ dPh @ Phinv @ H.conj().T))
         out[e] = np.real(psi.conj() @ term @ theta)
     return out
