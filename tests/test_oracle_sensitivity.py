@@ -117,6 +117,25 @@ def test_inversion_maps_gradient():
     assert np.allclose(g1[::-1, ::-1, ::-1], g2, rtol=1e-8, atol=1e-10 * np.abs(g1).max())
 
 
+def test_lattice_mirror_maps_gradient():
+    """FCC with a1 and a2 swapped is the Cartesian x <-> y mirror: with the design's first two
+    fractional axes and Q_1, Q_2 swapped, the eigenvalue is unchanged and its sensitivity field
+    swaps the same two axes (a transposed operand in the field synthesis would break this)."""
+    rng = np.random.default_rng(27)
+    rho = rng.uniform(0.2, 0.8, (5, 5, 5))
+    Q = np.array([0.21, 0.06, -0.13])
+    P1 = mixed.build("fcc", rho.shape, 1, rho, PH1, PH0, 3.0)
+    P2 = mixed.build("fcc", rho.shape, 1, np.transpose(rho, (1, 0, 2)), PH1, PH0, 3.0)
+    s1, s2 = mixed.solve_k(P1, Q, 5), mixed.solve_k(P2, Q[[1, 0, 2]], 5)
+    b = 4
+    assert abs(s1.lam[b] - s2.lam[b]) <= 1e-11 * s1.lam[b]
+    assert s1.lam[b] - s1.lam[b - 1] > 1e-3 * s1.lam[b]
+    g1 = sensitivity.voxel(P1, s1.lam[b], s1.theta[:, b], s1.s[:, b]).reshape(rho.shape)
+    g2 = sensitivity.voxel(P2, s2.lam[b], s2.theta[:, b], s2.s[:, b]).reshape(rho.shape)
+    assert np.allclose(np.transpose(g1, (1, 0, 2)), g2, rtol=1e-8, atol=1e-10 * np.abs(g1).max())
+    assert not np.allclose(g1, g2, rtol=1e-3)   # the field is not symmetric by itself
+
+
 def test_cluster_sum_is_basis_independent():
     """A degenerate pair at a high-symmetry point: the summed sensitivity is unchanged by a
     unitary rotation inside the pair."""
