@@ -1,0 +1,49 @@
+"""Host-side pieces of bench.py (CPU): the clock sampler's parsing of nvidia-smi lines, which decides
+which throttle reasons a run reports."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+class _DoneProcess:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _summary(lines):
+    cs = bench.ClockSampler(0)
+    cs.proc = _DoneProcess()
+    cs.lines = list(lines)
+    return cs.stop()
+
+
+def test_clock_lines_give_median_max_and_reasons():
+    quiet = "0, {sm}, 2070, 850.10, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+    capped = "0, 1980, 2070, 1398.70, 0x0000000000000004, Not Active, Not Active, Not Active, Active"
+    out = _summary([quiet.format(sm=2070), quiet.format(sm=2055), capped, "garbage", "",
+                    "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"])
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2055.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_each_slowdown_reason_is_reported():
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for i, name in enumerate(names):
+        flags = ["Not Active"] * 4
+        flags[i] = "Active"
+        out = _summary(["0, 1500, 2070, 900.0, 0x1, " + ", ".join(flags)])
+        assert out["reasons"] == [name]
+
+
+def test_no_samples_is_flagged():
+    assert _summary([])["reasons"] == ["no samples"]
+    cs = bench.ClockSampler(0)
+    assert cs.stop()["reasons"] == ["nvidia-smi unavailable"]
