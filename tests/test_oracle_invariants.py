@@ -82,15 +82,18 @@ def test_sc_point_group():
 def test_fcc_primitive_permutation_and_inversion():
     """Swapping a1 and a2 of the FCC primitive cell is the Cartesian x <-> y reflection; the
     design's first two fractional axes and Q_1, Q_2 swap with it.  Inversion maps s -> -s
-    and Q -> -Q."""
+    and Q -> -Q; the rotation about the cube diagonal cycles the axes and Q."""
     rng = np.random.default_rng(17)
     rho = rng.uniform(0, 1, (5, 5, 5))
     Q = np.array([0.19, 0.33, 0.07])
     base = mixed.bands(_problem("fcc", rho.shape, 1, rho), [Q], 8)[0]
     swap = mixed.bands(_problem("fcc", rho.shape, 1, np.transpose(rho, (1, 0, 2))), [Q[[1, 0, 2]]], 8)[0]
     inv = mixed.bands(_problem("fcc", rho.shape, 1, rho[::-1, ::-1, ::-1]), [-Q], 8)[0]
+    # the 3-fold rotation about the cube diagonal cycles a1, a2, a3
+    rot = mixed.bands(_problem("fcc", rho.shape, 1, np.transpose(rho, (1, 2, 0))), [Q[[1, 2, 0]]], 8)[0]
     assert np.allclose(base, swap, rtol=1e-11)
     assert np.allclose(base, inv, rtol=1e-11)
+    assert np.allclose(base, rot, rtol=1e-11)
 
 
 def test_bcc_primitive_point_group():
