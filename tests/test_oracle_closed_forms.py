@@ -54,6 +54,52 @@ def test_homogeneous_mixture_uses_interpolated_compliance():
     assert np.allclose(lam, ref, rtol=1e-12, atol=1e-12 * ref.max())
 
 
+
+def _mixture_speeds2(p1, p0, chi):
+    """Squared longitudinal and transverse speeds of the uniform mixture whose density and
+    compliance moduli f1 = (1 - 2 nu)/E, f2 = (1 + nu)/E are linear in chi."""
+    f1 = (1 - 2 * p0["nu"]) / p0["E"] + chi * ((1 - 2 * p1["nu"]) / p1["E"] - (1 - 2 * p0["nu"]) / p0["E"])
+    f2 = (1 + p0["nu"]) / p0["E"] + chi * ((1 + p1["nu"]) / p1["E"] - (1 + p0["nu"]) / p0["E"])
+    rho = p0["rho"] + chi * (p1["rho"] - p0["rho"])
+    Kb, mu = 1 / (3 * f1), 1 / (2 * f2)
+    return (Kb + 4 * mu / 3) / rho, mu / rho
+
+
+def test_uniform_mixture_power_law_p3():
+    """rho_e = 0.5 everywhere with p = 3: the material is the mixture at chi = 0.5^3 = 0.125
+    (not at rho = 0.5), and a uniform change of rho moves every eigenvalue by
+    d lambda/d chi * d chi/d rho with d chi/d rho = 3 * 0.5^2 = 0.75.  The element sensitivities
+    of one eigenpair therefore sum to that closed form; checked on the two transverse modes and the
+    longitudinal mode of the lowest plane wave at a generic wavevector (a wrong exponent, or chi
+    and d chi both taken linear, fails it)."""
+    from oracle import sensitivity
+    w = wl.homogeneous("sc", (4, 4, 4), 1, 9, 8, value=0.5)
+    w.penal = 3.0
+    P = mixed.from_workload(w)
+    assert np.allclose(P.chi, 0.125) and np.allclose(P.dchi, 0.75)
+    Q = np.array([0.13, 0.07, 0.21])   # generic: one shortest K, its modes apart from the rest
+    K = lat.wavevectors(P.T, Q, P.g)
+    k2 = (2 * np.pi) ** 2 * np.sum(K * K, axis=1)
+    cL2, cT2 = _mixture_speeds2(w.phase1, w.phase0, 0.125)
+    ref = np.sort(np.concatenate([k2 * cL2, k2 * cT2, k2 * cT2]))[:9]
+    lam, sols = mixed.bands(P, [Q], 9, keep=True)
+    assert np.allclose(lam[0], ref, rtol=1e-12, atol=1e-12 * ref.max())
+    # closed-form derivative along chi of the modes of the lowest plane wave (central difference
+    # of the closed form itself, exact to ~1e-10 for these smooth rational functions)
+    kmin = np.min(k2)
+    h = 1e-6
+    sp = _mixture_speeds2(w.phase1, w.phase0, 0.125 + h), _mixture_speeds2(w.phase1, w.phase0, 0.125 - h)
+    dL = kmin * (sp[0][0] - sp[1][0]) / (2 * h)
+    dT = kmin * (sp[0][1] - sp[1][1]) / (2 * h)
+    bL = int(np.argmin(np.abs(lam[0] - kmin * cL2)))   # the longitudinal mode, wherever it sorts
+    assert abs(lam[0][bL] - kmin * cL2) <= 1e-12 * ref.max()
+    assert np.all(np.abs(np.delete(lam[0], bL) - lam[0][bL]) > 1e-6 * lam[0][bL])  # isolated
+    sol = sols[0]
+    for b, d in ((0, dT), (1, dT), (bL, dL)):
+        total = np.sum(sensitivity.voxel(P, sol.lam[b], sol.theta[:, b], sol.s[:, b]))
+        assert abs(total - 0.75 * d) <= 1e-7 * abs(0.75 * d), (b, total, 0.75 * d)
+
+
 def _rytov_roots(k, d1, d2, c1, c2, Z1, Z2, wmax, count):
     def f(w):
         return (np.cos(w * d1 / c1) * np.cos(w * d2 / c2)
