@@ -52,6 +52,15 @@ extern "C" {
 #define PC_MIXED  1  /* split-BF16 tensor-core operator, FP32 block iteration,
                         FP64 Rayleigh-Ritz and stresses at the end */
 
+/* Degenerate clusters (pc_gap_and_grad, pc_gap_ks_and_grad): at a k-point, the bands whose
+ * eigenvalue lies within this relative distance of the extremal band's share its weight equally
+ * (the gradient of the cluster-mean eigenvalue, independent of the basis the solver picked inside
+ * the cluster).  The FP64 form resolves eigenvalues to about 1e-12; the mixed form's final FP64
+ * Rayleigh-Ritz step on FP32-converged vectors leaves symmetry-protected multiplets split by up to
+ * a few 1e-8 (its eigenvalue error), so it takes a wider window. */
+#define PC_CLUSTER_TOL_FP64   1e-8
+#define PC_CLUSTER_TOL_MIXED  1e-6
+
 /* Objective modes of pc_gap_and_grad. */
 #define PC_GAP_OMEGA      0  /* gap = 2(b-a)/(b+a) in omega = sqrt(lambda) (Results, note on gaps) */
 #define PC_GAP_LAMBDA     1  /* same in lambda = omega^2 (Methods, eq. obj) */
@@ -148,7 +157,8 @@ int pc_bands(pc_ctx* ctx, double* omega_dev, void* stream);
  * sensitivityew, diffOmega, diffPhi).  gap_dev: one double.  grad_dev: n0*n1*n2
  * doubles dG/drho_e, or NULL to skip the gradient.  The max/min pick the extremal
  * (k, band); equal values at different k take the lowest k; bands within a relative
- * 1e-8 of the extremal one at that k share its weight equally.  For PC_GRAD_ALLBANDS,
+ * PC_CLUSTER_TOL_FP64 / PC_CLUSTER_TOL_MIXED of the extremal one at that k share its weight
+ * equally.  For PC_GRAD_ALLBANDS,
  * w_dev holds nk*nbands weights, n_lower is ignored, gap_dev receives sum w*lambda
  * and grad_dev sum_{k,b} w[k,b] dlambda_{k,b}/drho_e.
  * The gradient stages, per CTA, the N coefficients of one field component and the
@@ -170,7 +180,8 @@ int pc_gap_and_grad(pc_ctx* ctx, int n_lower, int mode, const double* w_dev,
  *   b = -omega_ref (1/beta) log sum_k exp(-beta x_{k,n+1}),   gap = 2 (b - a) / (b + a),
  * a lower bound of the exact gap that tends to it as beta grows.  grad_dev (or NULL) receives
  * dgap/drho_e through the same adjoint as pc_gap_and_grad, with every k weighted; at each k
- * the bands within a relative 1e-8 of band n (and of band n+1) share its weight equally.
+ * the bands within the cluster window of pc_gap_and_grad of band n (and of band n+1) share its
+ * weight equally.
  * Errors: PC_ESTATE (pc_bands not run), PC_EINVAL (NULL gap_dev, n_lower out of
  * 1..nbands-1, beta not in (0, 1e12), the gradient's grid limit of pc_gap_and_grad),
  * PC_ECUDA. */
@@ -262,18 +273,20 @@ int pc_check_tensor_kernels(int what, int nk, int m, int nblk, int n3, double* r
  * For callers that may not allocate device memory once they are running: processes that
  * reserve their whole device-memory budget at start-up, loops that cannot afford the latency
  * or the implicit synchronisation of an allocation, and hosts whose allocator is not
- * available to library code.  Computes, without pc_create and without allocating, the SIMP
- * fields of a design and the structure factors of density and of the two compliance moduli
- * (Methods, eq. loop), exactly as pc_set_design does: sfac_dev receives 3 x (4M+1)^3 complex
- * values (interleaved re, im; density, f1 = (1-2nu)/E, f2 = (1+nu)/E), the same layout as
- * pc_export(PC_EXPORT_SFAC).  Reads n, M, phase0, phase1 and penal from params (the
- * structure factors in fractional coordinates do not depend on the lattice).
+ * available to library code.  Computes, without pc_create and without allocating, what the
+ * first step of pc_set_design computes: the SIMP fields of the design and its structure
+ * factors.  sfac_dev receives 3 x (4M+1)^3 complex values (interleaved re, im; density,
+ * f1 = (1-2nu)/E, f2 = (1+nu)/E), the array and layout pc_export(PC_EXPORT_SFAC) returns after
+ * pc_set_design.  Reads n, M, phase0, phase1 and penal from params, with the rules of pc_create
+ * (the structure factors in fractional coordinates do not depend on the lattice).
  *
  * Working space: one fixed 5 MiB array in device memory, which every GPU that loads this
  * library holds until the process exits.  It fits grids up to 40^3 voxels with M <= 5;
  * larger problems are rejected with PC_ETOOBIG before anything is enqueued.
  * The first call on a device looks up that array's device address (once per device, with
  * the device current), so make the first call on each device outside any stream capture.
+ * The address is kept for the life of the process: after a cudaDeviceReset of a device the
+ * library must be reloaded before this entry point is used there again.
  * All calls share the array and every call overwrites it: calls that may overlap on the
  * GPU (different streams, or threads, on one device) race and must be serialised by the
  * caller.  Densities outside [0, 1] are clamped.

@@ -14,6 +14,7 @@ PC_OK, PC_EINVAL, PC_EALIAS, PC_ENOMEM, PC_ECUDA, PC_ESTATE, PC_ENOCONV, PC_EDOM
 PC_SC, PC_BCC, PC_FCC = 0, 1, 2
 PC_FP64, PC_MIXED = 0, 1
 PC_GAP_OMEGA, PC_GAP_LAMBDA, PC_GRAD_ALLBANDS = 0, 1, 2
+PC_CLUSTER_TOL_FP64, PC_CLUSTER_TOL_MIXED = 1e-8, 1e-6
 PC_EXPORT_SFAC, PC_EXPORT_TOEP, PC_EXPORT_WINV, PC_EXPORT_EIGVEC, PC_EXPORT_LAMBDA, PC_EXPORT_WEIGHT = range(6)
 LATTICES = {"sc": PC_SC, "bcc": PC_BCC, "fcc": PC_FCC}
 

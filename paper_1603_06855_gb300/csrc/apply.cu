@@ -403,25 +403,6 @@ int launch_d2f(const double2* src, float2* dst, long long n, double scale, cudaS
   return PC_OK;
 }
 
-__global__ void k_r_f2d(const float* __restrict__ s, double* __restrict__ d, long long n) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) d[t] = (double)s[t];
-}
-__global__ void k_r_d2f(const double* __restrict__ s, float* __restrict__ d, long long n) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) d[t] = (float)s[t];
-}
-int launch_real_f2d(const float* src, double* dst, long long n, cudaStream_t s) {
-  k_r_f2d<<<cdiv(n, 256), 256, 0, s>>>(src, dst, n);
-  PC_LAUNCH_CHECK();
-  return PC_OK;
-}
-int launch_real_d2f(const double* src, float* dst, long long n, cudaStream_t s) {
-  k_r_d2f<<<cdiv(n, 256), 256, 0, s>>>(src, dst, n);
-  PC_LAUNCH_CHECK();
-  return PC_OK;
-}
-
 __global__ void k_scale_d2(double2* __restrict__ x, long long n, double s) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) { x[t].x *= s; x[t].y *= s; }

@@ -2,6 +2,9 @@
 #pragma once
 #include "common.cuh"
 
+// A phase accepted by pc_create: rho > 0, E > 0 (both finite), -1 < nu < 0.5.
+bool pc_material_ok(const pc_material& m);
+
 struct MaterialConsts {
   double penal;
   double rho0, rho1;   // mass density of phase0 / phase1
@@ -103,7 +106,6 @@ template <typename R> int launch_update(const UpdateArgs<R>& a, cudaStream_t s);
 // Tensor-core versions for FP32 data (tall_tc.cu); g_tc_tall = 0 selects the CUDA-core kernels.
 // Process-wide switches read by every launch, from any k-group thread.
 extern std::atomic<int> g_tc_tall;
-extern std::atomic<int> g_acc64;  // lobpcg.cu: FP64 accumulation in the FP32 Gram/update (experiments)
 int launch_gram_tc(const float2* const A[3], int na, const float2* const B[3], int nbk, int nk, int m, int n3,
                    float scale, float2* part, int max_split, float2* G, int* status, cudaStream_t s);
 int launch_update_tc(const UpdateArgs<float>& u, int* status, cudaStream_t s);
@@ -126,8 +128,6 @@ int launch_small_pdir(const typename cplx_t<R>::type* GO, const typename cplx_t<
                       const int* kdone, R abs_drop, typename cplx_t<R>::type* CP, cudaStream_t s);
 
 int launch_convert_f2d(const float2* src, double2* dst, long long n, cudaStream_t s);
-int launch_real_f2d(const float* src, double* dst, long long n, cudaStream_t s);
-int launch_real_d2f(const double* src, float* dst, long long n, cudaStream_t s);
 
 // Gap objective and adjoint.
 struct GapArgs {

@@ -13,7 +13,6 @@
 #define GRAM_SPLIT 8
 #define GRAM_LD 73   // odd row stride of the shared tiles (columns up to 72)
 
-std::atomic<int> g_acc64{0};  // experiment switch: FP64 accumulation in the FP32 Gram and update kernels
 
 // G_part[k][split] = A^H B over one row range; each of the 16 x 16 threads holds TILE x TILE outputs.  Shared tiles are double-buffered: the next
 // tile of GRAM_ROWS rows (16 in FP32, 8 in FP64: 37 KB of static shared memory either way)
@@ -126,18 +125,13 @@ int launch_gram(BlockList<R> A, int na, BlockList<R> B, int nbk, int nk, int m, 
                 typename cplx_t<R>::type* part, typename cplx_t<R>::type* G, cudaStream_t s, int* status) {
   if (na * m > 72 || nbk * m > 72 || na * m > 80) return PC_EINVAL;
   if constexpr (std::is_same<R, float>::value) {
-    if (g_tc_tall && status && !g_acc64) return launch_gram_tc(A.p, na, B.p, nbk, nk, m, n3, scale, part, GRAM_SPLIT, G, status, s);
+    if (g_tc_tall && status) return launch_gram_tc(A.p, na, B.p, nbk, nk, m, n3, scale, part, GRAM_SPLIT, G, status, s);
   }
   dim3 grid(nk, GRAM_SPLIT);
   // 16 x 16 threads, TILE x TILE outputs each: 2 x 2 covers up to 32 columns per side
   const bool small = na * m <= 32 && nbk * m <= 32;
-  if (g_acc64) {
-    if (small) k_gram<R, double, 2><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
-    else k_gram<R, double, 5><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
-  } else {
-    if (small) k_gram<R, R, 2><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
-    else k_gram<R, R, 5><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
-  }
+  if (small) k_gram<R, R, 2><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
+  else k_gram<R, R, 5><<<grid, 256, 0, s>>>(A, na, B, nbk, m, n3, part);
   PC_LAUNCH_CHECK();
   int nel = na * m * nbk * m;
   dim3 g2(cdiv(nel, 256), nk);
@@ -198,15 +192,9 @@ template <typename R> static int launch_update_cuda(const UpdateArgs<R>& a, cuda
   int nsum = a.identity_last ? a.nblk - 1 : a.nblk;
   if (nsum * a.m * a.mout > 72 * 24 || a.mout > 24) return PC_EINVAL;
   dim3 grid(cdiv(a.n3, 128), a.nk, a.ntrip);
-  if (g_acc64) {
-    if (a.mout <= 8) k_update<R, 8, double><<<grid, 128, 0, s>>>(a);
-    else if (a.mout <= 16) k_update<R, 16, double><<<grid, 128, 0, s>>>(a);
-    else k_update<R, 24, double><<<grid, 128, 0, s>>>(a);
-  } else {
-    if (a.mout <= 8) k_update<R, 8, R><<<grid, 128, 0, s>>>(a);
-    else if (a.mout <= 16) k_update<R, 16, R><<<grid, 128, 0, s>>>(a);
-    else k_update<R, 24, R><<<grid, 128, 0, s>>>(a);
-  }
+  if (a.mout <= 8) k_update<R, 8, R><<<grid, 128, 0, s>>>(a);
+  else if (a.mout <= 16) k_update<R, 16, R><<<grid, 128, 0, s>>>(a);
+  else k_update<R, 24, R><<<grid, 128, 0, s>>>(a);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
@@ -215,7 +203,7 @@ template <typename R> static int launch_update_cuda(const UpdateArgs<R>& a, cuda
 // kernel takes one set per launch; the tensor-core kernel (FP32) takes both in one pass.
 template <typename R> int launch_update(const UpdateArgs<R>& a, cudaStream_t s) {
   if constexpr (std::is_same<R, float>::value) {
-    if (g_tc_tall && a.status && !g_acc64) return launch_update_tc(a, a.status, s);
+    if (g_tc_tall && a.status) return launch_update_tc(a, a.status, s);
   }
   int rc = launch_update_cuda<R>(a, s);
   if (rc || !a.C2nd) return rc;

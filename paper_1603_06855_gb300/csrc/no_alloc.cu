@@ -8,6 +8,8 @@
 // them the SIMP fields and the three structure factors of a design without pc_create: its
 // working space is the file-scope array below, which every device that loads this library
 // holds until the process exits.
+#include <cmath>
+#include <mutex>
 #include "kernels.h"
 
 // Working space of the allocation-free path: SIMP fields (3 ne), chi and dchi (2 ne), and the
@@ -26,11 +28,15 @@ __global__ void k_sfac3(const double2* __restrict__ t2, int n0, int M, double in
 namespace {
 const int kMaxDevices = 64;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mu;  // calls from several host threads look the address up once
 
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array on the current device, looked up once per device (the
+// set-up step of the first call there).  A cudaDeviceReset destroys the module that holds the
+// array, so the recorded address is stale afterwards; the header says so.
 int scratch_for_current_device(unsigned char** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PC_ECUDA;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
@@ -48,12 +54,13 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 extern "C" int pc_structure_factors_noalloc(const pc_params* p, const double* rho_dev, double* sfac_dev,
                                             void* stream) {
+  // the same parameter rules as pc_create (the lattice and the band fields are not read)
   if (!p || !rho_dev || !sfac_dev) return PC_EINVAL;
   if (p->M < 1 || p->M > 5) return PC_EINVAL;
   for (int i = 0; i < 3; ++i)
-    if (p->n[i] < 1) return PC_EINVAL;
-  if (!(p->phase0.E > 0 && p->phase1.E > 0 && p->phase0.rho > 0 && p->phase1.rho > 0)) return PC_EINVAL;
-  if (!(p->penal >= 1.0)) return PC_EINVAL;
+    if (p->n[i] < 1 || p->n[i] > 256) return PC_EINVAL;
+  if (!pc_material_ok(p->phase0) || !pc_material_ok(p->phase1)) return PC_EINVAL;
+  if (!(p->penal >= 1.0) || !std::isfinite(p->penal)) return PC_EINVAL;
   const int M2 = 2 * p->M + 1;
   for (int i = 0; i < 3; ++i)
     if (p->n[i] < M2) return PC_EALIAS;

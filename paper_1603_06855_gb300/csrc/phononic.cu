@@ -97,12 +97,7 @@ struct pc_ctx {
   long long ph_count[PH_COUNT] = {};
   long long launch_base = 0;
   unsigned long long seed = 0;  // PC_INIT_SEED: offset of the start-block perturbation
-  int small32 = 1;              // projected problems of the mixed iteration in FP32 (PC_SMALL_FP32=0: FP64)
-  int apply64 = 0;              // PC_APPLY64=1: FP64 operator inside the mixed iteration (experiments)
   int refresh = 40;             // iterations between recomputations of A X, Omega X (PC_REFRESH)
-  int use_tc = 1;               // PC_TC=0: FP32 CUDA-core operator GEMM instead of tensor cores
-  double2 *sGA = nullptr, *sGO = nullptr, *sC = nullptr, *sCP = nullptr;  // FP64 widened projected problems
-  double* slam = nullptr;
 };
 
 // Number of k groups of the mixed form's block iteration for nk k-points (1: one stream).
@@ -173,7 +168,7 @@ template <typename T> static void dfree(T*& p) {
   p = nullptr;
 }
 
-static bool material_ok(const pc_material& m) {
+bool pc_material_ok(const pc_material& m) {
   return m.rho > 0 && m.E > 0 && m.nu > -1.0 && m.nu < 0.5 && std::isfinite(m.rho) && std::isfinite(m.E);
 }
 
@@ -233,7 +228,6 @@ static void free_kset(pc_ctx* c) {
   dfree(c->gpartd); dfree(c->GAd); dfree(c->GOd); dfree(c->Cd);
   dfree(c->lamd); dfree(c->lam_nd); dfree(c->rnormd); dfree(c->actived);
   dfree(c->weights); dfree(c->pairs); dfree(c->npairs); dfree(c->adj_t2);
-  dfree(c->sGA); dfree(c->sGO); dfree(c->sC); dfree(c->sCP); dfree(c->slam);
   for (auto& t : c->tcg)
     if (t) { tc_plan_destroy(t); t = nullptr; }
   if (c->tc) { tc_plan_destroy(c->tc); c->tc = nullptr; }
@@ -272,7 +266,7 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
   if (p->M < 1 || p->M > 5) return PC_EINVAL;
   for (int i = 0; i < 3; ++i)
     if (p->n[i] < 1 || p->n[i] > 256) return PC_EINVAL;
-  if (!material_ok(p->phase0) || !material_ok(p->phase1)) return PC_EINVAL;
+  if (!pc_material_ok(p->phase0) || !pc_material_ok(p->phase1)) return PC_EINVAL;
   if (!(p->penal >= 1.0) || !std::isfinite(p->penal)) return PC_EINVAL;
   if (p->precision != PC_FP64 && p->precision != PC_MIXED) return PC_EINVAL;
   if (p->tol < 0 || p->max_iter < 0) return PC_EINVAL;
@@ -288,24 +282,14 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
   {
     const char* dbg = getenv("PC_DEBUG");
     c->debug = (dbg && dbg[0] == '1') ? 1 : 0;
-    const char* acc = getenv("PC_ACC64");
-    g_acc64 = (acc && acc[0] == '1') ? 1 : 0;
     const char* rf = getenv("PC_REFRESH");
     if (rf && atoi(rf) > 0) c->refresh = atoi(rf);
-    const char* tcv = getenv("PC_TC");
-    c->use_tc = (tcv && tcv[0] == '0') ? 0 : 1;
-    const char* a64 = getenv("PC_APPLY64");
-    c->apply64 = (a64 && a64[0] == '1') ? 1 : 0;
-    const char* s32 = getenv("PC_SMALL_FP32");
-    c->small32 = (s32 && s32[0] == '0') ? 0 : 1;
     const char* sd = getenv("PC_INIT_SEED");
     c->seed = sd ? strtoull(sd, nullptr, 10) : 0ull;
     const char* sp = getenv("PC_SPLIT");
     c->split = (sp && sp[0] == '0') ? 0 : 1;
     const char* kg = getenv("PC_KGROUPS");
     if (kg && atoi(kg) >= 2 && atoi(kg) <= kMaxGroups) c->groups = atoi(kg);
-    const char* tt = getenv("PC_TC_TALL");
-    g_tc_tall = (tt && tt[0] == '0') ? 0 : 1;
   }
   // Default residual targets: 1e-8 for the FP64 form; 3e-4 for the FP32 iteration of the mixed
   // form, whose final FP64 Rayleigh-Ritz step makes eigenvalue errors quadratic in the residual
@@ -451,11 +435,6 @@ extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
   rc |= dalloc(&c->weights, (size_t)nk * c->nb);
   rc |= dalloc(&c->pairs, (size_t)nk * c->nb);
   rc |= dalloc(&c->npairs, 1);
-  rc |= dalloc(&c->sGA, g);
-  rc |= dalloc(&c->sGO, g);
-  rc |= dalloc(&c->sC, g);
-  rc |= dalloc(&c->sCP, g);
-  rc |= dalloc(&c->slam, nvec);
   rc |= dalloc(&c->adj_t2, (size_t)nk * c->nb * 9 * c->M2 * c->prm.n[1] * c->prm.n[2]);
   if (rc == PC_OK && c->prm.precision == PC_MIXED) {
     c->tc = tc_plan_create(N, (int)nvec, c->status);
@@ -556,19 +535,11 @@ static int apply_fp64(pc_ctx* c, const double2* X, double2* AX, double2* OX, int
 }
 
 // Nondimensional A' X and Omega' X for FP32 vectors (vector v at k = v / m of Q): the split-BF16
-// tensor-core path when available (PC_TC=0 selects the FP32 CUDA-core GEMM instead).
+// tensor-core path; the FP32 CUDA-core GEMM only where the tensor-core plan could not be set up.
 static int apply_fp32(pc_ctx* c, const float2* X, float2* AX, float2* OX, int nvec, int m, const double* Q,
                       cudaStream_t s, TcPlan* plan = nullptr) {
   if (!plan) plan = c->tc;
-  if (c->apply64) {  // experiment switch: FP64 operator on widened FP32 vectors
-    const long long n = (long long)nvec * 3 * c->N;
-    int rc = launch_convert_f2d(X, c->Xd, n, s);
-    if (!rc) rc = apply_fp64(c, c->Xd, c->AXd, c->OXd, nvec, m, Q, c->cA, 1.0 / c->sO, c->Ed, c->Sd, s);
-    if (!rc) rc = launch_d2f(c->AXd, AX, n, 1.0, s);
-    if (!rc) rc = launch_d2f(c->OXd, OX, n, 1.0, s);
-    return rc;
-  }
-  if (c->use_tc && plan && tc_available(plan)) {
+  if (plan && tc_available(plan)) {
     if (!c->tc_ready) {
       int rc = tc_prepare_operators(c->tc, c->W, c->T, c->cA, 1.0 / c->sO, s);
       if (rc) return rc;
@@ -639,56 +610,24 @@ static UpdateArgs<R> upd(pc_ctx* c, int nk, int nblk, int identity_last, const v
 // The projected problems (Rayleigh-Ritz pencil, conjugate-direction coefficients and the
 // Cholesky-QR of the search directions) of the mixed form's block iteration take FP32
 // Gram matrices; they are solved in FP32 (their inputs carry FP32 accuracy, and an FP64
-// solve costs ~60x more on this part's FP64 units).  PC_SMALL_FP32=0 widens them to FP64
-// (for experiments).  The final Rayleigh-Ritz step always runs in FP64 on FP64 Grams.
+// solve costs ~60x more on this part's FP64 units).  The final Rayleigh-Ritz step always runs
+// in FP64 on FP64 Grams.
 template <typename R> struct SmallTol;
 template <> struct SmallTol<double> { static constexpr double pdir_abs = 1e-26; };
-template <> struct SmallTol<float> { static constexpr double pdir_abs = 1e-12; };
+template <> struct SmallTol<float> { static constexpr float pdir_abs = 1e-12f; };
 
 template <typename R>
 static int small_rr_any(pc_ctx* c, int nk, const typename Ops<R>::C2* GA, const typename Ops<R>::C2* GO, int n, int m,
-                        const int* kdone, R* lam, typename Ops<R>::C2* cX, typename Ops<R>::C2* cP, cudaStream_t s);
-template <>
-int small_rr_any<double>(pc_ctx* c, int nk, const double2* GA, const double2* GO, int n, int m, const int* kdone,
-                         double* lam, double2* cX, double2* cP, cudaStream_t s) {
-  int rc = launch_small_rr<double>(GA, GO, n, m, nk, Ops<double>::drop_small, kdone, lam, cX, c->status, s);
-  if (!rc && cP) rc = launch_small_pdir<double>(GO, cX, n, m, nk, kdone, SmallTol<double>::pdir_abs, cP, s);
-  return rc;
-}
-template <>
-int small_rr_any<float>(pc_ctx* c, int nk, const float2* GA, const float2* GO, int n, int m, const int* kdone,
-                        float* lam, float2* cX, float2* cP, cudaStream_t s) {
-  if (c->small32) {
-    int rc = launch_small_rr<float>(GA, GO, n, m, nk, Ops<float>::drop_small, kdone, lam, cX, c->status, s);
-    if (!rc && cP) rc = launch_small_pdir<float>(GO, cX, n, m, nk, kdone, (float)SmallTol<float>::pdir_abs, cP, s);
-    return rc;
-  }
-  const long long nn = (long long)nk * n * n;
-  int rc = launch_convert_f2d(GA, c->sGA, nn, s);
-  if (!rc) rc = launch_convert_f2d(GO, c->sGO, nn, s);
-  if (!rc) rc = launch_real_f2d(lam, c->slam, (long long)nk * m, s);
-  if (!rc) rc = launch_small_rr<double>(c->sGA, c->sGO, n, m, nk, (double)Ops<float>::drop_small, kdone, c->slam,
-                                        c->sC, c->status, s);
-  if (!rc && cP) rc = launch_small_pdir<double>(c->sGO, c->sC, n, m, nk, kdone, SmallTol<float>::pdir_abs, c->sCP, s);
-  if (!rc) rc = launch_d2f(c->sC, cX, (long long)nk * n * m, 1.0, s);
-  if (!rc && cP) rc = launch_d2f(c->sCP, cP, (long long)nk * n * m, 1.0, s);
-  if (!rc) rc = launch_real_d2f(c->slam, lam, (long long)nk * m, s);
+                        const int* kdone, R* lam, typename Ops<R>::C2* cX, typename Ops<R>::C2* cP, cudaStream_t s) {
+  int rc = launch_small_rr<R>(GA, GO, n, m, nk, Ops<R>::drop_small, kdone, lam, cX, c->status, s);
+  if (!rc && cP) rc = launch_small_pdir<R>(GO, cX, n, m, nk, kdone, SmallTol<R>::pdir_abs, cP, s);
   return rc;
 }
 template <typename R>
 static int small_chol_any(pc_ctx* c, int nk, const typename Ops<R>::C2* G, int m, typename Ops<R>::C2* T,
-                          cudaStream_t s);
-template <>
-int small_chol_any<double>(pc_ctx* c, int nk, const double2* G, int m, double2* T, cudaStream_t s) {
-  return launch_small_chol<double>(G, m, nk, Ops<double>::drop_small, nullptr, 0, 0.0, T, s);
-}
-template <>
-int small_chol_any<float>(pc_ctx* c, int nk, const float2* G, int m, float2* T, cudaStream_t s) {
-  if (c->small32) return launch_small_chol<float>(G, m, nk, Ops<float>::drop_small, nullptr, 0, 0.0f, T, s);
-  int rc = launch_convert_f2d(G, c->sGO, (long long)nk * m * m, s);
-  if (!rc) rc = launch_small_chol<double>(c->sGO, m, nk, (double)Ops<float>::drop_small, nullptr, 0, 0.0, c->sC, s);
-  if (!rc) rc = launch_d2f(c->sC, T, (long long)nk * m * m, 1.0, s);
-  return rc;
+                          cudaStream_t s) {
+  (void)c;
+  return launch_small_chol<R>(G, m, nk, Ops<R>::drop_small, nullptr, 0, (R)0, T, s);
 }
 
 // The batched block iteration (all k at once).  Per iteration and k:
@@ -994,7 +933,7 @@ extern "C" int pc_bands(pc_ctx* c, double* omega, void* stream) {
   PC_CUDA_TRY(cudaEventRecord(c->ev0, s));
   int sl = ph_begin(c, PH_LOOP, 0.0, s);
   int rc;
-  bool split = c->split && c->prm.precision == PC_MIXED && c->use_tc && c->small32 && !c->apply64 && c->tc &&
+  bool split = c->split && c->prm.precision == PC_MIXED && c->tc &&
                tc_available(c->tc) && kgroups(c, c->nk) >= 2;
   for (int g = 1; split && g < kgroups(c, c->nk); ++g) split = c->tcg[g] && tc_available(c->tcg[g]);
   if (split) {
@@ -1043,7 +982,7 @@ static int gap_and_grad_impl(pc_ctx* c, int n_lower, int mode, double beta, cons
   g.lam = c->lam_nd;
   g.nk = c->nk; g.nb = c->nb; g.n_lower = n_lower; g.mode = mode;
   g.lref = c->lref;
-  g.rel_tol = 1e-8;
+  g.rel_tol = c->prm.precision == PC_MIXED ? PC_CLUSTER_TOL_MIXED : PC_CLUSTER_TOL_FP64;
   g.ks_beta = beta;
   g.w_user = w;
   g.gap_out = gap;

@@ -21,7 +21,8 @@
 
 using namespace tcx;
 
-std::atomic<int> g_tc_tall{1};  // tensor-core Gram and update kernels for FP32 data (0: CUDA cores)
+std::atomic<int> g_tc_tall{1};  // tensor-core Gram and update kernels for FP32 data (0: CUDA cores,
+                                // switched only by pc_check_tensor_kernels for its reference run)
 
 namespace {
 

@@ -10,7 +10,9 @@
 
 namespace tcx {
 
-constexpr long long WAIT_LIMIT = 1ll << 24;  // try_wait polls before giving up (seconds)
+// Polls of mbarrier.try_wait before a wait gives up (a count, not a time: each poll may itself
+// suspend the thread for a short, hardware-defined interval).  Far above any legitimate wait.
+constexpr long long WAIT_LIMIT = 1ll << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 

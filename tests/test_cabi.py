@@ -96,3 +96,24 @@ def test_mma_step_rejects_bad_arguments():
                 dict(lo=None), dict(up=None), dict(it=-1), dict(xmax=0.0), dict(xmin=2.0),
                 dict(xmin=float("nan")), dict(xmax=float("inf"))):
         assert call(**bad) == B.PC_EINVAL, bad
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(phase1=dict(rho=1.0, E=1.0, nu=0.5)), 1), (dict(phase0=dict(rho=1.0, E=float("nan"), nu=0.3)), 1),
+    (dict(phase0=dict(rho=float("inf"), E=1.0, nu=0.3)), 1), (dict(phase1=dict(rho=1.0, E=1.0, nu=-1.0)), 1),
+    (dict(penal=float("inf")), 1), (dict(penal=0.5), 1), (dict(M=0), 1), (dict(M=6), 1),
+    (dict(n=(300, 8, 8)), 1), (dict(n=(8, 0, 8)), 1),
+    (dict(n=(8, 4, 8), M=2), 2),
+    (dict(n=(48, 48, 48), M=2), 9), (dict(n=(64, 64, 64)), 9),
+])
+def test_noalloc_rejects_bad_parameters_on_host(kw, code):
+    """pc_structure_factors_noalloc applies pc_create's parameter rules and its own size limit
+    before any CUDA call (the placeholder pointers below are never dereferenced)."""
+    import ctypes
+    B = _lib()
+    lib = B.load()
+    buf = ctypes.create_string_buffer(64)
+    p = _params(**kw)
+    assert lib.pc_structure_factors_noalloc(ctypes.byref(p), ctypes.addressof(buf), ctypes.addressof(buf),
+                                            None) == code
+    assert lib.pc_structure_factors_noalloc(ctypes.byref(p), None, ctypes.addressof(buf), None) == B.PC_EINVAL

@@ -3,10 +3,11 @@ and grids from 16^3 to 40^3, 48 k-points and 20 bands each, mixed form.
 
 Every design runs through the library (all 48 k-points: with this many the block iteration
 runs as concurrent k groups); each must finish with PC_OK and ascending, finite frequencies.
-One design per (lattice, N) bucket is checked at two sampled k-points: against the FP64
-oracle for N <= 343, and against the library's FP64 form (itself held to 1e-9 of the oracle
-on the smaller configurations) for N = 729 and 1331, where the dense oracle needs minutes per
-k-point.  Tolerance: 1e-6 relative, |w - w_ref| / max(w_ref, 0.05 max w_ref).
+One design per (lattice, N) bucket, the one with the smallest voxel grid (the dense oracle's
+element sums grow with the grid; the library's path does not change with it), is checked
+against the FP64 oracle at two sampled k-points.  Tolerance: 1e-6 relative,
+|w - w_ref| / max(w_ref, 0.05 max w_ref).  The oracle needs about 20 s per sampled k at
+N = 1331 (7986 x 7986 compliance block).
 """
 import numpy as np
 import pytest
@@ -47,24 +48,23 @@ def _err(got, ref):
 
 def test_uneven_batch32(B):
     designs = wl.batch32_mixed()
-    seen = set()
+    pick = {}
+    for i, w in enumerate(designs):
+        key = (w.lattice, (2 * w.M + 1) ** 3)
+        if key not in pick or np.prod(w.n) < np.prod(designs[pick[key]].n):
+            pick[key] = i
+    assert len(pick) == 12, pick
+    checked = set(pick.values())
     worst = {}
-    for w in designs:
+    for i, w in enumerate(designs):
         om, st = _run(B, w, B.PC_MIXED)
         assert st.status == B.PC_OK, (w.name, B.pc_strerror(st.status))
         assert np.all(np.isfinite(om)) and np.all(np.diff(om, axis=1) >= 0), w.name
-        N = (2 * w.M + 1) ** 3
-        if (w.lattice, N) in seen:
+        if i not in checked:
             continue
-        seen.add((w.lattice, N))
-        if N <= 343:
-            P = mixed.from_workload(w)
-            lam_ref = mixed.bands(P, w.Q[SAMPLE_K], w.nbands)
-            ref = mixed.omega(lam_ref)
-        else:
-            ref, st64 = _run(B, w, B.PC_FP64, Q=w.Q[SAMPLE_K])
-            assert st64.status == B.PC_OK, (w.name, B.pc_strerror(st64.status))
+        P = mixed.from_workload(w)
+        ref = mixed.omega(mixed.bands(P, w.Q[SAMPLE_K], w.nbands))
         worst[w.name] = _err(om[SAMPLE_K], ref)
-    assert len(seen) == 12, seen
+    assert len(worst) == 12, worst
     bad = {k: v for k, v in worst.items() if not v <= 1e-6}
     assert not bad, bad

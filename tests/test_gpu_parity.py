@@ -8,6 +8,8 @@ Tolerances (stated per result):
   |w - w_ref| / max(w_ref, 0.05 max w_ref); Gamma zero modes |lambda| <= 1e-9 lambda_max;
 * gap: same relative bound as the frequencies; gradient: relative L2 1e-5 (FP64) and 1e-4 (mixed).
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -20,6 +22,11 @@ pytestmark = pytest.mark.gpu
 
 TOL_W = {"fp64": 1e-9, "mixed": 1e-6}
 TOL_G = {"fp64": 1e-5, "mixed": 1e-4}
+
+
+def ctol(B, precision):
+    """The library's degenerate-cluster window for the form (the oracle takes the same)."""
+    return B.PC_CLUSTER_TOL_FP64 if precision == "fp64" else B.PC_CLUSTER_TOL_MIXED
 
 
 @pytest.fixture(scope="module")
@@ -58,6 +65,14 @@ def canonical_k(Q):
                 out[i] = out[j]
                 break
     return out
+
+
+@functools.lru_cache(maxsize=None)
+def sc16_oracle():
+    w = wl.sc16_grf()
+    P = mixed.from_workload(w)
+    lam_ref, sols = mixed.bands(P, w.Q, w.nbands, keep=True)
+    return P, lam_ref, sols
 
 
 def run_gpu(w, precision, Q=None, **kw):
@@ -159,17 +174,20 @@ def test_bands_match_oracle(B, name, precision):
     s.close()
 
 
+@pytest.mark.parametrize("mode", ["omega", "lambda"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_gap_and_gradient_match_oracle(B, precision):
-    """SC 16^3 random field (M = 2, 30 k): gap(3,4) and gap(6,7) in the omega form and the full 4096-element gradient."""
+def test_gap_and_gradient_match_oracle(B, precision, mode):
+    """SC 16^3 random field (M = 2, 30 k): gap(3,4) and gap(6,7) in the omega form (Results, note
+    on normalized band gaps) and in the lambda form of eq. obj (PC_GAP_LAMBDA), and the full
+    4096-element gradient of each."""
     w = wl.sc16_grf()
-    P = mixed.from_workload(w)
-    lam_ref, sols = mixed.bands(P, w.Q, w.nbands, keep=True)
+    P, lam_ref, sols = sc16_oracle()
     s, om, st = run_gpu(w, precision)
+    omode, cmode = (ogap.MODE_OMEGA, B.PC_GAP_OMEGA) if mode == "omega" else (ogap.MODE_LAMBDA, B.PC_GAP_LAMBDA)
     for n_lower in w.gaps:
-        r = ogap.gap(lam_ref, n_lower)
+        r = ogap.gap(lam_ref, n_lower, mode=omode, rel_tol=ctol(B, precision))
         g_ref = sensitivity.weighted(P, sols, r.weights)
-        gap, grad = s.gap_and_grad(n_lower)
+        gap, grad = s.gap_and_grad(n_lower, cmode)
         gap = gap.cpu().numpy()[0]
         grad = grad.cpu().numpy().ravel()
         assert abs(gap - r.gap) <= TOL_W[precision] * 4 * abs(r.gap) + 1e-12
@@ -214,7 +232,7 @@ def test_bcc24_sampled_k(B, precision):
     lam_ref, sols = mixed.bands(P, Q, w.nbands, keep=True)
     s, om, st = run_gpu(w, precision, Q=Q)
     assert omega_err(om, mixed.omega(lam_ref), lam_ref) <= TOL_W[precision]
-    r = ogap.gap(lam_ref, 6)
+    r = ogap.gap(lam_ref, 6, rel_tol=ctol(B, precision))
     g_ref = sensitivity.weighted(P, sols, r.weights)
     gap, grad = s.gap_and_grad(6)
     rel = np.linalg.norm(grad.cpu().numpy().ravel() - g_ref) / np.linalg.norm(g_ref)
@@ -310,15 +328,41 @@ def test_smooth_ks_gap_and_gradient(B, precision):
     (every k weighted) against the oracle's KS gap: gap within the frequency tolerance, gradient
     within the gradient tolerance (relative L2)."""
     w = wl.sc16_grf()
-    P = mixed.from_workload(w)
-    lam_ref, sols = mixed.bands(P, w.Q, w.nbands, keep=True)
+    P, lam_ref, sols = sc16_oracle()
     omega_ref = 2.0 * np.pi / w.a * np.sqrt(w.phase1["E"] / w.phase1["rho"])
     s, om, st = run_gpu(w, precision)
     for beta in (20.0, 200.0):
-        r = ogap.ks_gap(lam_ref, 6, beta, omega_ref)
+        r = ogap.ks_gap(lam_ref, 6, beta, omega_ref, rel_tol=ctol(B, precision))
         g_ref = sensitivity.weighted(P, sols, r.weights)
         gap, grad = s.gap_ks_and_grad(6, beta)
         assert abs(gap.item() - r.gap) <= TOL_W[precision] * abs(r.gap), (gap.item(), r.gap)
         rel = np.linalg.norm(grad.cpu().numpy().ravel() - g_ref) / np.linalg.norm(g_ref)
         assert rel <= TOL_G[precision], rel
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_iteration_cap_reports_nonconvergence(B, precision):
+    """max_iter = 3 on the SC 16^3 random field: the block iteration stops far above its residual
+    target, pc_get_stats reports PC_ENOCONV with every k-point still open, and the outputs are
+    written anyway (finite, ascending frequencies from the FP64 Rayleigh-Ritz step on the last
+    block; a gap and a finite gradient)."""
+    w = wl.sc16_grf()
+    s = solver_for(w, precision, max_iter=3)
+    s.set_design(torch.from_numpy(w.rho.ravel()).cuda())
+    om = torch.full((w.nk, w.nbands), float("nan"), dtype=torch.float64, device="cuda")
+    s.bands(out=om)
+    gap, grad = s.gap_and_grad(6)
+    st = s.stats()
+    assert st.status == B.PC_ENOCONV, B.pc_strerror(st.status)
+    assert st.iterations == 3 and st.unconverged_k > 0
+    om = om.cpu().numpy()
+    assert np.all(np.isfinite(om)) and np.all(np.diff(om, axis=1) >= 0)
+    assert np.isfinite(gap.item()) and np.all(np.isfinite(grad.cpu().numpy()))
+    s.close()
+    # the same design without the cap converges
+    s = solver_for(w, precision)
+    s.set_design(torch.from_numpy(w.rho.ravel()).cuda())
+    s.bands()
+    assert s.stats().status == B.PC_OK
     s.close()
