@@ -23,6 +23,9 @@ It is the plain dense definition of the method, written from the paper:
                      forms they reduce to.
 * ``mma``         -- one step of the method of moving asymptotes for the box-constrained
                      design problem (Methods, eq. ``topopt``; the paper names no optimizer).
+* ``projection``  -- the design parametrisation: reduced design field, Heaviside projection
+                     and the SC mirror symmetry, with their chain rule (Methods, "Topology
+                     optimization formulation"; Results, "Topology optimized structures").
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms
 (homogeneous media, Rytov laminates), invariants (Gamma zero modes, time
@@ -30,4 +33,4 @@ reversal, translation, point group, inversion), brute-force finite differences
 and the numbers the paper prints (band edges of its optimized cells, sphere-inclusion
 gaps, the 1-D laminate optimum).
 """
-from . import lattice, mixed, gap, sensitivity, mma  # noqa: F401
+from . import lattice, mixed, gap, sensitivity, mma, projection  # noqa: F401
