@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--cpu-k", type=int, default=2, help="k-points in the oracle sample")
@@ -183,6 +183,26 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# DRAM traffic per launch of the dominant kernels, from one ncu capture each (dram__bytes_read.sum +
+# dram__bytes_write.sum; the summaries are under profiles/).  Each entry holds the SHA-256 of the
+# kernel's source file when it was captured: once that file changes, the figure is stale and the
+# bench reports null.
+TRAFFIC = {}
+
+
+def traffic_per_launch(kernel: str):
+    t = TRAFFIC.get(kernel)
+    if not t:
+        return None
+    import hashlib
+    path = os.path.join(ROOT, "paper_1603_06855_gb300", "csrc", t["source"])
+    try:
+        sha = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return t["bytes"] if sha == t["sha256"] else None
+
+
 def measured_peaks() -> dict:
     """HBM copy bandwidth and bf16 GEMM throughput measured on this GPU pool (JSON at the repo root)."""
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
@@ -320,28 +340,40 @@ def main():
     steps_ = args.steps
     fam = {}
 
-    def add(name, ms, amount, launches, bound, peak, unit, source, traffic_key=None):
-        if ms <= 0 or peak is None:
+    def add(name, kernel, ms, amount, launches, bound, peak, unit, source):
+        if ms <= 0 or peak is None or amount <= 0:
             return
         achieved = amount / (ms * 1e-3) / (1e12 if unit == "TFLOP/s" else 1e9)
-        fam[name] = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak, "traffic": None, "peak_source": source,
+        fam[name] = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak, "traffic": traffic_per_launch(kernel), "peak_source": source,
                      "launches_timed": int(launches), "share_of_step": ms / ms_pf}
 
     # Gram products and basis updates: split-BF16 tensor-core kernels that read each FP32 operand
     # once and write the result once, so HBM bound (algorithmic bytes / measured copy bandwidth)
     if peaks.get("hbm_gbs"):
-        add("gram_AhB", st_pf.ms_gram, st_pf.gram_bytes, st_pf.gram_launches, "hbm", peaks["hbm_gbs"], "GB/s",
-            "MEASURED_PEAKS.json hbm_gbs")
-        add("basis_update_SC", st_pf.ms_update, st_pf.update_bytes, st_pf.update_launches, "hbm", peaks["hbm_gbs"],
+        add("gram_AhB", "k_tc_gram", st_pf.ms_gram, st_pf.gram_bytes, st_pf.gram_launches, "hbm", peaks["hbm_gbs"],
             "GB/s", "MEASURED_PEAKS.json hbm_gbs")
-    # operator apply: split-BF16 tensor-core GEMM, six bf16 products per FP32-accurate product
+        add("basis_update_SC", "k_tc_update", st_pf.ms_update, st_pf.update_bytes, st_pf.update_launches, "hbm",
+            peaks["hbm_gbs"], "GB/s", "MEASURED_PEAKS.json hbm_gbs")
+    # operator apply: split-BF16 tensor-core GEMM; the method's flops against the raw sustained
+    # BF16 peak, and beside it against that peak / 6 (six bf16 slice products per FP32-accurate one)
     if peaks.get("bf16_tflops_sustained"):
-        add("iteration_operator_apply", st_pf.ms_iter_apply, st_pf.iter_apply_flops, st_pf.iter_apply_calls, "tensor",
-            peaks["bf16_tflops_sustained"] / 6.0, "TFLOP/s",
-            "MEASURED_PEAKS.json bf16_tflops_sustained / 6 (six bf16 slice products per FP32-accurate product)")
-    add("fp64_rayleigh_ritz_gemm", st_pf.ms_rr_gemm, st_pf.rr_gemm_flops, st_pf.rr_gemm_launches, "alu",
-        fp64_peak / 1e3, "TFLOP/s", "measured FP64 FMA throughput (pc_probe) on this GPU")
+        add("iteration_operator_apply", "k_tc_gemm", st_pf.ms_iter_apply, st_pf.iter_apply_flops,
+            st_pf.iter_apply_calls, "tensor", peaks["bf16_tflops_sustained"], "TFLOP/s",
+            "MEASURED_PEAKS.json bf16_tflops_sustained")
+        if "iteration_operator_apply" in fam:
+            f = fam["iteration_operator_apply"]
+            f["frac_of_split_bf16_peak"] = f["achieved"] / (peaks["bf16_tflops_sustained"] / 6.0)
+    add("fp64_rayleigh_ritz_gemm", "k_gemm<double>", st_pf.ms_rr_gemm, st_pf.rr_gemm_flops, st_pf.rr_gemm_launches,
+        "alu", fp64_peak / 1e3, "TFLOP/s", "measured FP64 FMA throughput (pc_probe) on this GPU")
+    # projected eigenproblems (Cholesky, reduction, Jacobi sweeps as executed) against FP32 FMA; the
+    # family time also holds the small Cholesky-QR and conjugate-direction kernels
+    add("projected_problems", "k_small_rr32", st_pf.ms_small, st_pf.small_flops, 0, "alu", fp32_peak / 1e3,
+        "TFLOP/s", "measured FP32 FMA throughput (pc_probe) on this GPU")
+    # adjoint synthesis and reduction (FP32 in the mixed form)
+    add("adjoint", "k_adj_synth12+k_adj_reduce", st_pf.ms_grad_kernels,
+        prof_steps * st_pf.grad_pairs * st_pf.grad_flops_per_pair, 2 * prof_steps, "alu", fp32_peak / 1e3,
+        "TFLOP/s", "measured FP32 FMA throughput (pc_probe) on this GPU")
     dom = max(fam, key=lambda k: fam[k]["share_of_step"])
     roofline = dict(fam[dom])
     roofline["of"] = "measured"
@@ -391,6 +423,7 @@ def main():
                                   "fp64_rayleigh_ritz": st_pf.ms_final_rr / prof_steps,
                                   "rr_gemm": st_pf.ms_rr_gemm / prof_steps,
                                   "adjoint": st_pf.ms_grad_kernels / prof_steps,
+                                  "host_idle_between_iterations": st_pf.ms_host_idle / prof_steps,
                                   "last_set_design": st_pf.ms_setup, "last_bands": st_pf.ms_bands,
                                   "last_gap_and_grad": st_pf.ms_grad},
             "timed_run": {"k_halves_on_two_streams": True, "last_bands_ms": st_mx.ms_bands,

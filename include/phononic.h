@@ -119,6 +119,14 @@ typedef struct {
   double update_bytes;     /* algorithmic bytes: inputs read once, outputs written once */
   double ms_iteration_loop; /* device time of the whole block iteration (pc_bands before its FP64 step) */
   double ms_final_rr;      /* device time of the FP64 Rayleigh-Ritz step */
+  double small_flops;      /* algorithmic flops of the FP32 projected eigenproblems (mixed form) solved
+                              while profiling: per problem of n coordinates, n_k kept, s Jacobi sweeps,
+                              (32/3) n^3 + s n_k (n_k - 1) 12 (n_k + n) */
+  long long grad_pairs;    /* weighted (k, band) pairs of the last pc_gap_and_grad / pc_gap_ks_and_grad */
+  double grad_flops_per_pair; /* algorithmic flops of the adjoint per weighted pair:
+                              72 ((2M+1)^3 n2 + (2M+1)^2 n1 n2 + (2M+1) n0 n1 n2) */
+  double ms_host_idle;     /* stream idle time while the host reads the convergence count of each block
+                              iteration and enqueues the next one (profiling; summed over the k groups) */
 } pc_stats;
 
 /* Creates a context: validates the parameters and allocates every per-design

@@ -70,6 +70,10 @@ class pc_stats(ctypes.Structure):
         ("update_bytes", ctypes.c_double),
         ("ms_iteration_loop", ctypes.c_double),
         ("ms_final_rr", ctypes.c_double),
+        ("small_flops", ctypes.c_double),
+        ("grad_pairs", ctypes.c_longlong),
+        ("grad_flops_per_pair", ctypes.c_double),
+        ("ms_host_idle", ctypes.c_double),
     ]
 
 

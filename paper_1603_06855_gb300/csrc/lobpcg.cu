@@ -632,7 +632,6 @@ int launch_small_rr(const typename cplx_t<R>::type* GA, const typename cplx_t<R>
   return PC_OK;
 }
 template int launch_small_rr<double>(const double2*, const double2*, int, int, int, double, const int*, double*, double2*, int*, cudaStream_t);
-template int launch_small_rr<float>(const float2*, const float2*, int, int, int, float, const int*, float*, float2*, int*, cudaStream_t);
 
 // Cholesky-QR transform: T = D Li^H with zero columns for dropped coordinates.
 template <typename R>

@@ -18,6 +18,7 @@
 #include <atomic>
 #include <mutex>
 #include <thread>
+#include <type_traits>
 #include <vector>
 #include "kernels.h"
 #include "gemm_tc.h"
@@ -27,7 +28,7 @@ std::atomic<long long> g_pc_launches{0};
 
 // Per-phase device timing (pc_set_profiling): event pairs recorded on the caller's stream.
 enum { PH_RR_GEMM = 0, PH_ITER_APPLY = 1, PH_SMALL = 2, PH_GRAD = 3, PH_GRAM = 4, PH_UPDATE = 5, PH_LOOP = 6,
-       PH_FINAL = 7, PH_COUNT = 8 };
+       PH_FINAL = 7, PH_IDLE = 8, PH_COUNT = 9 };
 // Smallest k group worth its own stream, and the most groups (mixed form, see pc_bands).
 constexpr int kSplitMinK = 16;
 constexpr int kMaxGroups = 6;
@@ -62,6 +63,8 @@ struct pc_ctx {
   double2 *t1 = nullptr, *t2s = nullptr, *sfac = nullptr, *T = nullptr, *W = nullptr, *gj_row = nullptr, *gj_col = nullptr;
   float2 *Wf = nullptr, *Tf = nullptr;  // scaled FP32 copies (mixed path)
   int* status = nullptr;
+  double* small_flops = nullptr;  // device: algorithmic flops of the FP32 projected problems while profiling
+  double grad_flops_per_pair = 0;  // algorithmic flops of the adjoint per weighted (k, band)
   // per k-set
   double* Q = nullptr;
   void* blk[15] = {nullptr};     // X AX OX W AW OW P AP OP Xn AXn OXn Pn APn OPn (R precision)
@@ -241,7 +244,7 @@ extern "C" void pc_destroy(pc_ctx* c) {
   free_kset(c);
   dfree(c->fields); dfree(c->dchi); dfree(c->chi); dfree(c->chi_mean);
   dfree(c->t1); dfree(c->t2s); dfree(c->sfac); dfree(c->T); dfree(c->W); dfree(c->gj_row); dfree(c->gj_col);
-  dfree(c->Wf); dfree(c->Tf); dfree(c->status);
+  dfree(c->Wf); dfree(c->Tf); dfree(c->status); dfree(c->small_flops);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   for (cudaEvent_t e : {c->ev_s0, c->ev_s1, c->ev_g0, c->ev_g1})
@@ -346,6 +349,12 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
     const char* sh = getenv("PC_PREC_SHIFT");
     c->pr.shift_scale = (sh && atof(sh) > 0) ? atof(sh) : 0.25;
   }
+  {
+    // adjoint per weighted (k, band): 9 fields synthesised along axis 2 (M2^3 n2 complex
+    // multiply-adds), axis 1 (M2^2 n1 n2) and axis 0 inside the voxel reduction (M2 n0 n1 n2)
+    const double m2 = M2, n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
+    c->grad_flops_per_pair = 8.0 * 9.0 * (m2 * m2 * m2 * n2 + m2 * m2 * n1 * n2 + m2 * n0 * n1 * n2);
+  }
   c->pr.two_pi_sq_V_over_sA = two_pi * two_pi * c->V / c->sA;
   c->pr.half_lref_V_over_sA = 0.5 * c->lref * c->V / c->sA;
 
@@ -364,12 +373,13 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
   rc |= dalloc(&c->gj_row, 2 * 32 * (size_t)N);              // blocked Gauss-Jordan: old pivot rows
   rc |= dalloc(&c->gj_col, 2 * 32 * ((size_t)N + 32));       // pivot-block inverses, column panels
   rc |= dalloc(&c->status, 1);
+  rc |= dalloc(&c->small_flops, 1);
   if (p->precision == PC_MIXED) {
     rc |= dalloc(&c->Wf, 2 * NN);
     rc |= dalloc(&c->Tf, NN);
   }
   if (rc != PC_OK) { pc_destroy(c); return PC_ENOMEM; }
-  if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
+  if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess || cudaMemset(c->small_flops, 0, sizeof(double)) != cudaSuccess ||
       cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
       cudaEventCreate(&c->ev_s0) != cudaSuccess || cudaEventCreate(&c->ev_s1) != cudaSuccess ||
       cudaEventCreate(&c->ev_g0) != cudaSuccess || cudaEventCreate(&c->ev_g1) != cudaSuccess ||
@@ -619,7 +629,12 @@ template <> struct SmallTol<float> { static constexpr float pdir_abs = 1e-12f; }
 template <typename R>
 static int small_rr_any(pc_ctx* c, int nk, const typename Ops<R>::C2* GA, const typename Ops<R>::C2* GO, int n, int m,
                         const int* kdone, R* lam, typename Ops<R>::C2* cX, typename Ops<R>::C2* cP, cudaStream_t s) {
-  int rc = launch_small_rr<R>(GA, GO, n, m, nk, Ops<R>::drop_small, kdone, lam, cX, c->status, s);
+  int rc;
+  if constexpr (std::is_same<R, float>::value)
+    rc = launch_small_rr32(GA, GO, n, m, nk, Ops<R>::drop_small, kdone, lam, cX, c->status,
+                           c->profiling ? c->small_flops : nullptr, s);
+  else
+    rc = launch_small_rr<R>(GA, GO, n, m, nk, Ops<R>::drop_small, kdone, lam, cX, c->status, s);
   if (!rc && cP) rc = launch_small_pdir<R>(GO, cX, n, m, nk, kdone, SmallTol<R>::pdir_abs, cP, s);
   return rc;
 }
@@ -715,6 +730,9 @@ static int run_block_iteration(pc_ctx* c, KSet& ks) {
     TRY(launch_resnorm<R>(AX, OX, lam, nk, m, nb, n3, c->prm.tol, rnorm, active, kdone, ks.d_unconv, s, sbest,
                           ssince));
     PC_CUDA_TRY(cudaMemcpyAsync(ks.h_unconv, ks.d_unconv, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // While profiling, the stream's idle gap while the host waits for the count and enqueues the
+    // next step: from the completion of the copy to the next work the host enqueues.
+    const int idle_slot = ph_begin(c, PH_IDLE, 0.0, s);
     PC_CUDA_TRY(cudaStreamSynchronize(s));
     ks.unconv = *ks.h_unconv;
     if (c->debug) {
@@ -740,6 +758,7 @@ static int run_block_iteration(pc_ctx* c, KSet& ks) {
         fprintf(stderr, "\n");
       }
     }
+    ph_end(c, idle_slot, s);
     if (ks.unconv == 0) break;
     TRY(launch_precond<R>(AX, OX, lam, active, kdone, nk, m, nb, c->geom, Qk, c->pr, c->chi_mean, Wb, s));
     // W <- W - X (OX^H W) - P (OP^H W), before the operator is applied
@@ -1086,7 +1105,15 @@ extern "C" int pc_get_stats(pc_ctx* c, pc_stats* out) {
   out->update_flops = c->ph_flops[PH_UPDATE];
   out->update_bytes = c->ph_bytes[PH_UPDATE];
   out->ms_iteration_loop = c->ph_ms[PH_LOOP];
+  PC_CUDA_TRY(cudaMemcpy(&out->small_flops, c->small_flops, sizeof(double), cudaMemcpyDeviceToHost));
+  out->grad_flops_per_pair = c->grad_flops_per_pair;
+  if (c->have_grad && c->npairs) {
+    int np = 0;
+    PC_CUDA_TRY(cudaMemcpy(&np, c->npairs, sizeof(int), cudaMemcpyDeviceToHost));
+    out->grad_pairs = np;
+  }
   out->ms_final_rr = c->ph_ms[PH_FINAL];
+  out->ms_host_idle = c->ph_ms[PH_IDLE];
   out->status = st;
   return st;
 }
@@ -1103,6 +1130,7 @@ extern "C" int pc_set_profiling(pc_ctx* c, int on) {
   PC_CUDA_TRY(cudaDeviceSynchronize());
   ph_collect(c);
   for (int i = 0; i < PH_COUNT; ++i) { c->ph_ms[i] = 0; c->ph_flops[i] = 0; c->ph_bytes[i] = 0; c->ph_count[i] = 0; }
+  PC_CUDA_TRY(cudaMemset(c->small_flops, 0, sizeof(double)));
   c->profiling = on ? 1 : 0;
   return PC_OK;
 }
