@@ -214,6 +214,53 @@ int pc_gap_ks_and_grad(pc_ctx* ctx, int n_lower, double beta, double* gap_dev, d
 int pc_mma_step(long long n, double* x_dev, const double* df_dev, double* xold1_dev, double* xold2_dev,
                 double* low_dev, double* upp_dev, int iter, double xmin, double xmax, void* stream);
 
+/* --- Design parametrisation (Methods, "Topology optimization formulation", the passage after
+ * eq. sensitivityew; Results, "Topology optimized structures") ---
+ *
+ * The densities rho_e passed to pc_set_design as a closed-form function of free design
+ * variables x, and the chain rule that turns d(objective)/d(rho_e) (grad_dev of pc_gap_and_grad
+ * or pc_gap_ks_and_grad) into d(objective)/dx:
+ *   phi   = x, or for octant = 1 (SC cells only) the image of x under the mirror symmetries
+ *           a -> n_d - 1 - a of the design grid (x holds one octant, (n_d/2)^3 values);
+ *   mu_e  = sum_a w_ea phi_a / sum_a w_ea over the design nodes a within `radius` of element e's
+ *           centroid (Cartesian distance to the nearest periodic image), w_ea = radius - distance;
+ *           design node a sits at the centre of the spacing^3 element block a (spacing 2: the
+ *           paper's reduced design field with variables at twice the element size);
+ *   rho_e = 1 - exp(-beta mu_e) + mu_e exp(-beta)   (Heaviside projection; beta is raised by the
+ *           caller's continuation, the paper starts at beta = 1).
+ * Layouts: x C-ordered over the design grid (n_i / spacing per axis) or its octant; rho over the
+ * element grid n0 x n1 x n2 (the layout of pc_set_design). */
+typedef struct pc_design pc_design;
+typedef struct {
+  int spacing;     /* design nodes every `spacing` elements along each axis: 1 or 2 */
+  double radius;   /* projection radius, metres (the paper's 1.4 % of the cell is read as 1.4 element edges) */
+  int octant;      /* 1: SC mirror symmetry, the free variables are one octant of the design grid */
+} pc_design_params;
+
+/* Builds the weight table of the map for the cell's lattice, a and grid n (other fields of cell
+ * are not read) and allocates its device state.
+ * Errors: PC_EINVAL (NULL, bad lattice or a, spacing not 1 or 2 or not dividing every n_i,
+ * n_i outside 1..256, radius not positive or so large that it reaches a node's periodic image,
+ * an element with no node within the radius, octant on a non-SC lattice or an odd design grid),
+ * PC_ENOMEM, PC_ECUDA.  *out is NULL on error. */
+int pc_design_create(const pc_params* cell, const pc_design_params* dp, pc_design** out);
+
+/* Number of free variables (length of x), or -1 for NULL. */
+long long pc_design_nvars(const pc_design* d);
+
+/* rho_dev (n0 n1 n2 doubles) <- the densities of x_dev (nvars doubles in [0, 1]) at sharpness
+ * beta > 0.  Keeps d rho / d mu of this call for pc_design_backprop.  Device pointers, stream
+ * ordered.  Errors: PC_EINVAL (NULL, beta not positive and finite), PC_ECUDA. */
+int pc_design_project(pc_design* d, const double* x_dev, double beta, double* rho_dev, void* stream);
+
+/* g_x_dev (nvars doubles) <- d(objective)/dx from g_rho_dev = d(objective)/d(rho_e) (n0 n1 n2
+ * doubles), at the x and beta of the last pc_design_project on this map (stream ordered after it).
+ * Errors: PC_EINVAL (NULL), PC_ECUDA. */
+int pc_design_backprop(pc_design* d, const double* g_rho_dev, double* g_x_dev, void* stream);
+
+/* Frees the map.  NULL is allowed. */
+void pc_design_destroy(pc_design* d);
+
 /* Synchronises the device and fills *out; returns out->status as well. */
 int pc_get_stats(pc_ctx* ctx, pc_stats* out);
 

@@ -118,12 +118,16 @@ class DesignMap:
     def phi(self, x):
         return mirror_expand(x, self.nd) if self.octant else np.asarray(x, float).ravel()
 
+    def mu(self, x) -> np.ndarray:
+        """The filtered field; a convex combination of values in [0, 1], clamped to [0, 1] only to
+        remove rounding excursions."""
+        return np.clip(self.F @ self.phi(x), 0.0, 1.0)
+
     def forward(self, x, beta: float) -> np.ndarray:
-        mu = self.F @ self.phi(x)
-        return heaviside(mu, beta).reshape(self.n)
+        return heaviside(self.mu(x), beta).reshape(self.n)
 
     def backward(self, x, beta: float, g_rho) -> np.ndarray:
         """dG/dx from dG/drho (chain rule through projection, filter and mirror)."""
-        mu = self.F @ self.phi(x)
+        mu = self.mu(x)
         g_phi = self.F.T @ (np.asarray(g_rho, float).ravel() * dheaviside(mu, beta))
         return mirror_fold(g_phi, self.nd) if self.octant else g_phi

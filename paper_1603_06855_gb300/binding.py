@@ -39,6 +39,10 @@ class pc_params(ctypes.Structure):
     ]
 
 
+class pc_design_params(ctypes.Structure):
+    _fields_ = [("spacing", ctypes.c_int), ("radius", ctypes.c_double), ("octant", ctypes.c_int)]
+
+
 class pc_stats(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int),
@@ -80,7 +84,8 @@ class pc_stats(ctypes.Structure):
 EXPORTED = ["pc_create", "pc_set_kpoints", "pc_set_design", "pc_bands", "pc_gap_and_grad", "pc_gap_ks_and_grad",
             "pc_get_stats",
             "pc_clear_status", "pc_set_profiling", "pc_probe", "pc_destroy", "pc_strerror", "pc_export",
-            "pc_apply_operator", "pc_check_tensor_kernels", "pc_structure_factors_noalloc", "pc_mma_step"]
+            "pc_apply_operator", "pc_check_tensor_kernels", "pc_structure_factors_noalloc", "pc_mma_step",
+            "pc_design_create", "pc_design_nvars", "pc_design_project", "pc_design_backprop", "pc_design_destroy"]
 
 _lib = None
 
@@ -113,9 +118,16 @@ def load(path: str = LIB_PATH):
     lib.pc_structure_factors_noalloc.argtypes = [ctypes.POINTER(pc_params), P, P, P]
     lib.pc_check_tensor_kernels.argtypes = [I, I, I, I, I, ctypes.POINTER(ctypes.c_double)]
     lib.pc_mma_step.argtypes = [LL, P, P, P, P, P, P, I, D, D, P]
+    lib.pc_design_create.argtypes = [ctypes.POINTER(pc_params), ctypes.POINTER(pc_design_params), ctypes.POINTER(P)]
+    lib.pc_design_nvars.argtypes = [P]
+    lib.pc_design_project.argtypes = [P, P, D, P, P]
+    lib.pc_design_backprop.argtypes = [P, P, P, P]
+    lib.pc_design_destroy.argtypes = [P]
     for name in EXPORTED:
-        if name not in ("pc_destroy", "pc_strerror"):
+        if name not in ("pc_destroy", "pc_strerror", "pc_design_destroy", "pc_design_nvars"):
             getattr(lib, name).restype = I
+    lib.pc_design_nvars.restype = LL
+    lib.pc_design_destroy.restype = None
     _lib = lib
     return lib
 
@@ -244,3 +256,41 @@ def pc_check_tensor_kernels(what: int, nk: int, m: int, nblk: int, n3: int) -> f
 def pc_structure_factors_noalloc(params: pc_params, rho_ptr: int, sfac_ptr: int, stream: int = 0) -> int:
     """Allocation-free structure factors (return code; 0 on success)."""
     return load().pc_structure_factors_noalloc(ctypes.byref(params), rho_ptr, sfac_ptr, stream)
+
+
+def make_design_params(spacing: int = 2, radius: float = 0.0, octant: bool = False) -> pc_design_params:
+    dp = pc_design_params()
+    dp.spacing = int(spacing)
+    dp.radius = float(radius)
+    dp.octant = 1 if octant else 0
+    return dp
+
+
+def pc_design_create_rc(cell: pc_params, dp: pc_design_params):
+    """(return code, handle or 0)."""
+    h = ctypes.c_void_p()
+    rc = load().pc_design_create(ctypes.byref(cell), ctypes.byref(dp), ctypes.byref(h))
+    return rc, (h.value or 0)
+
+
+def pc_design_create(cell: pc_params, dp: pc_design_params) -> int:
+    rc, h = pc_design_create_rc(cell, dp)
+    _check(rc, "pc_design_create")
+    return h
+
+
+def pc_design_nvars(d: int) -> int:
+    return int(load().pc_design_nvars(d))
+
+
+def pc_design_project(d: int, x_ptr: int, beta: float, rho_ptr: int, stream: int = 0) -> None:
+    _check(load().pc_design_project(d, x_ptr, float(beta), rho_ptr, stream), "pc_design_project")
+
+
+def pc_design_backprop(d: int, g_rho_ptr: int, g_x_ptr: int, stream: int = 0) -> None:
+    _check(load().pc_design_backprop(d, g_rho_ptr, g_x_ptr, stream), "pc_design_backprop")
+
+
+def pc_design_destroy(d: int) -> None:
+    if d:
+        load().pc_design_destroy(d)

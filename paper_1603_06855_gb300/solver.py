@@ -115,6 +115,73 @@ def gap(rho: torch.Tensor, solver: BandSolver, n_lower: int, mode: int = B.PC_GA
     return GapFn.apply(rho, solver, n_lower, mode)
 
 
+class DesignMap:
+    """Reduced design field -> element densities (pc_design_*): linear-weight average of the
+    design nodes within the radius, Heaviside projection at sharpness beta, optional SC octant
+    symmetry.  The radius defaults to 1.4 element edges (|a_1| / n_1)."""
+
+    def __init__(self, lattice, n, spacing: int = 2, radius: float | None = None, octant: bool = False,
+                 a: float = 1.0, device="cuda"):
+        import math
+        self.device = torch.device(device)
+        self.n = tuple(int(v) for v in n)
+        if radius is None:
+            edge = {"sc": 1.0, "bcc": math.sqrt(3.0) / 2.0, "fcc": math.sqrt(2.0) / 2.0}[lattice] * a / self.n[0]
+            radius = 1.4 * edge
+        cell = B.make_params(lattice, self.n, 1, 1, {"rho": 1.0, "E": 1.0, "nu": 0.3},
+                             {"rho": 1.0, "E": 1.0, "nu": 0.3}, a=a)
+        self.handle = B.pc_design_create(cell, B.make_design_params(spacing, radius, octant))
+        self.nvars = B.pc_design_nvars(self.handle)
+
+    def _stream(self) -> int:
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def project(self, x: torch.Tensor, beta: float, out: torch.Tensor | None = None) -> torch.Tensor:
+        x = x.detach().to(self.device, torch.float64).contiguous()
+        if x.numel() != self.nvars:
+            raise ValueError("x must hold nvars values")
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        self._x = x
+        B.pc_design_project(self.handle, x.data_ptr(), beta, out.data_ptr(), self._stream())
+        return out
+
+    def backprop(self, g_rho: torch.Tensor) -> torch.Tensor:
+        """d/dx from d/drho, at the x and beta of the last project()."""
+        g_rho = g_rho.detach().to(self.device, torch.float64).contiguous()
+        gx = torch.empty(self.nvars, dtype=torch.float64, device=self.device)
+        B.pc_design_backprop(self.handle, g_rho.data_ptr(), gx.data_ptr(), self._stream())
+        return gx
+
+    def close(self):
+        if getattr(self, "handle", 0):
+            B.pc_design_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ProjectFn(torch.autograd.Function):
+    """x (nvars) -> rho (n0, n1, n2) through a DesignMap at sharpness beta; backward by the
+    map's chain rule (the forward is re-run first, so interleaved calls stay consistent)."""
+
+    @staticmethod
+    def forward(ctx, x, dmap: DesignMap, beta: float):
+        ctx.save_for_backward(x.detach().clone())
+        ctx.dmap, ctx.beta = dmap, beta
+        return dmap.project(x, beta)
+
+    @staticmethod
+    def backward(ctx, g):
+        (x,) = ctx.saved_tensors
+        ctx.dmap.project(x, ctx.beta)
+        return ctx.dmap.backprop(g), None, None
+
+
 class MMA:
     """Device state of the design update of eq. topopt (method of moving asymptotes with the
     bounds as the only constraint) for n variables; each step is one pc_mma_step launch."""
@@ -140,21 +207,41 @@ class MMA:
         self.iteration += 1
 
 
-def maximize_gap(solver: BandSolver, rho: torch.Tensor, n_lower: int, beta: float, steps: int):
+def heaviside_schedule(step: int, every: int, start: float = 1.0, factor: float = 2.0, cap: float = 64.0) -> float:
+    """Continuation of the projection sharpness: start (the paper's beta = 1), multiplied by
+    factor every `every` steps, at most cap."""
+    return min(cap, start * factor ** (step // max(1, every)))
+
+
+def maximize_gap(solver: BandSolver, rho: torch.Tensor, n_lower: int, beta: float, steps: int,
+                 design: DesignMap | None = None, beta_every: int = 0):
     """Optimization loop of eq. topopt on the smooth (KS) gap between bands n_lower and n_lower+1:
-    band structure, gap and adjoint gradient, then one MMA design update, `steps` times.  Returns
-    the final design (n0, n1, n2) and the gap before each step and after the last."""
+    band structure, gap and adjoint gradient, then one MMA design update, `steps` times.  Without
+    a design map the variables are the densities (rho, shape n); with one they are its free
+    variables (rho, nvars values in [0, 1]), the densities are their projection at the sharpness
+    heaviside_schedule(step, beta_every) (beta_every = 0: 1 throughout) and the gradient is carried
+    back through the map.  Returns the final variables and the gap before each step and after
+    the last."""
     x = rho.detach().to(solver.device, torch.float64).contiguous().clone().view(-1)
     opt = MMA(x.numel(), device=solver.device)
     history = []
-    for _ in range(steps):
-        solver.set_design(x)
+
+    def evaluate(step, need_grad):
+        if design is None:
+            solver.set_design(x)
+        else:
+            hb = heaviside_schedule(step, beta_every) if beta_every > 0 else 1.0
+            solver.set_design(design.project(x, hb))
         solver.bands()
-        g, grad = solver.gap_ks_and_grad(n_lower, beta)
+        g, grad = solver.gap_ks_and_grad(n_lower, beta, need_grad=need_grad)
+        if need_grad and design is not None:
+            grad = design.backprop(grad)
+        return g, grad
+
+    for step in range(steps):
+        g, grad = evaluate(step, True)
         history.append(float(g.item()))
         opt.step(x, grad.view(-1))
-    solver.set_design(x)
-    solver.bands()
-    g, _ = solver.gap_ks_and_grad(n_lower, beta, need_grad=False)
+    g, _ = evaluate(steps, False)
     history.append(float(g.item()))
-    return x.view(solver.n), history
+    return (x.view(solver.n) if design is None else x), history

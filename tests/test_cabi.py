@@ -117,3 +117,20 @@ def test_noalloc_rejects_bad_parameters_on_host(kw, code):
     assert lib.pc_structure_factors_noalloc(ctypes.byref(p), ctypes.addressof(buf), ctypes.addressof(buf),
                                             None) == code
     assert lib.pc_structure_factors_noalloc(ctypes.byref(p), None, ctypes.addressof(buf), None) == B.PC_EINVAL
+
+
+@pytest.mark.parametrize("lattice,n,spacing,rad,octant", [
+    ("sc", (8, 8, 8), 3, 2.0, 0), ("sc", (9, 8, 8), 2, 2.0, 0), ("bcc", (8, 8, 8), 2, 2.0, 1),
+    ("sc", (10, 10, 10), 2, 2.0, 1),   # the octant needs an even design grid (5 nodes per axis)
+    ("sc", (8, 8, 8), 2, 0.3, 0),      # no node within the radius
+    ("sc", (8, 8, 8), 2, 7.0, 0),      # the radius reaches a node's periodic image
+    ("sc", (8, 8, 8), 2, -1.0, 0), ("sc", (8, 8, 8), 2, 2.0, 2),
+])
+def test_design_create_rejects_bad_parameters(lattice, n, spacing, rad, octant):
+    """pc_design_create validates on the host before allocating anything."""
+    B = _lib()
+    cell = _params(lattice=lattice, n=n)
+    dp = B.make_design_params(spacing, rad / n[0], bool(octant))
+    dp.octant = octant
+    rc, h = B.pc_design_create_rc(cell, dp)
+    assert rc == B.PC_EINVAL and h == 0

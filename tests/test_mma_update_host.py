@@ -174,3 +174,67 @@ def test_maximize_gap_loop_matches_oracle_loop(cpu_solver_layer):
     assert np.allclose(hist, ref, rtol=1e-12, atol=0)
     assert tuple(x.shape) == w.n and np.abs(x.numpy().ravel() - r).max() <= 1e-13
     assert np.array_equal(rho_in.numpy(), rho0)  # the caller's design is not modified in place
+
+
+def test_heaviside_schedule():
+    from paper_1603_06855_gb300.solver import heaviside_schedule
+    assert [heaviside_schedule(s, 2) for s in range(8)] == [1, 1, 2, 2, 4, 4, 8, 8]
+    assert heaviside_schedule(100, 1) == 64.0
+
+
+def test_maximize_gap_through_design_map_matches_oracle_loop(cpu_solver_layer):
+    """The loop on free design variables: every step projects them (reduced field, SC octant,
+    beta from the continuation), evaluates the smooth gap on the densities and chains its gradient
+    back through the map; the map and the solver are answered by the oracle on CPU tensors."""
+    from oracle import projection
+    S = cpu_solver_layer
+    w = wl.sc8_binary_cube()
+    dm = projection.DesignMap("sc", w.n, spacing=2, radius=2.5 / 8, octant=True)
+    rng = np.random.default_rng(85)
+    x0 = rng.uniform(0.3, 0.7, dm.nvars)
+    beta = 50.0
+    wref = 2 * np.pi * np.sqrt(w.phase1["E"] / w.phase1["rho"])
+
+    def evaluate(r):
+        P = mixed.build(w.lattice, w.n, w.M, r.reshape(w.n), w.phase1, w.phase0, w.penal)
+        lam, sols = mixed.bands(P, w.Q, w.nbands, keep=True)
+        res = og.ks_gap(lam, 3, beta, omega_ref=wref)
+        return res.gap, sensitivity.weighted(P, sols, res.weights)
+
+    class OracleSolver:
+        device = torch.device("cpu")
+        n = w.n
+
+        def set_design(self, rho):
+            self.rho = rho.detach().numpy().copy()
+
+        def bands(self):
+            pass
+
+        def gap_ks_and_grad(self, n_lower, b, need_grad=True):
+            g, grad = evaluate(self.rho)
+            return torch.tensor([g], dtype=torch.float64), torch.from_numpy(grad.reshape(w.n)) if need_grad else None
+
+    class OracleDesign:
+        betas = []
+
+        def project(self, x, hb):
+            self.x, self.hb = x.numpy().copy(), hb
+            self.betas.append(hb)
+            return torch.from_numpy(dm.forward(self.x, hb))
+
+        def backprop(self, g):
+            return torch.from_numpy(dm.backward(self.x, self.hb, g.numpy()))
+
+    des = OracleDesign()
+    x, hist = S.maximize_gap(OracleSolver(), torch.from_numpy(x0.copy()), 3, beta, 4, design=des, beta_every=2)
+    assert des.betas == [1.0, 1.0, 2.0, 2.0, 4.0]
+    r, st, ref = x0.copy(), mma.MMAState(), []
+    for step in range(5):
+        hb = S.heaviside_schedule(step, 2)
+        g, grad = evaluate(dm.forward(r, hb))
+        ref.append(g)
+        if step < 4:
+            r = mma.step(r, dm.backward(r, hb, grad), st)
+    assert np.allclose(hist, ref, rtol=1e-12, atol=0)
+    assert x.shape == (dm.nvars,) and np.abs(x.numpy() - r).max() <= 1e-13
