@@ -47,6 +47,11 @@ extern "C" {
 /* Largest wavevector count of one context (pc_set_kpoints). */
 #define PC_MAX_KPOINTS 65535
 
+/* Material interpolation between the phases (pc_params.law). */
+#define PC_LAW_COMPLIANCE 0  /* density and the compliance moduli (1-2nu)/E, (1+nu)/E linear in chi */
+#define PC_LAW_YOUNG      1  /* Methods, eq. combinematerial read literally: Young's modulus and Poisson's
+                                ratio linear in chi, each element the isotropic material they give */
+
 /* Arithmetic of the eigensolver. */
 #define PC_FP64   0  /* every step in FP64 on CUDA cores */
 #define PC_MIXED  1  /* split-BF16 tensor-core operator, FP32 block iteration,
@@ -86,6 +91,7 @@ typedef struct {
   int precision;        /* PC_FP64 | PC_MIXED */
   double tol;           /* relative residual target of the block iteration (0: default, 1e-8 FP64, 3e-4 mixed) */
   int max_iter;         /* iteration cap (0: default); hitting it sets PC_ENOCONV */
+  int law;              /* PC_LAW_COMPLIANCE (0, default) | PC_LAW_YOUNG; density is linear in chi either way */
 } pc_params;
 
 typedef struct {
@@ -291,11 +297,28 @@ const char* pc_strerror(int code);
 #define PC_EXPORT_EIGVEC 3  /* nk x nbands x 3N complex: eigenvectors, theta^H Omega theta = 1, SI */
 #define PC_EXPORT_LAMBDA 4  /* nk x nbands doubles: eigenvalues lambda = omega^2, SI */
 #define PC_EXPORT_WEIGHT 5  /* nk x nbands doubles: gap weights dG/dlambda of the last pc_gap_and_grad */
+#define PC_EXPORT_BLOCK  6  /* nk x block x 3N complex: the final Ritz block of the last pc_bands (bands
+                               and guard vectors, nondimensional; the start block pc_import_block takes) */
 
 /* Copies an internal array to host memory (synchronous).  Returns the number of
  * doubles the array holds in *count; copies only when host != NULL and
  * capacity >= *count.  Errors: PC_EINVAL (bad which), PC_ESTATE (not computed yet). */
 int pc_export(pc_ctx* ctx, int which, double* host, long long capacity, long long* count);
+
+/* Warm start across designs (not in the paper, which solves every design from scratch): with
+ * on = 1, each pc_bands starts its block iteration from the final Ritz block of the previous
+ * pc_bands of this context (the bands and guard vectors of every k), when there is one for the
+ * current k-points, instead of from the plane-wave start block; pc_set_kpoints discards it.  In an
+ * optimization loop the next design is close to the last, so fewer iterations are needed.  The
+ * results are the same eigenpairs to the iteration's tolerance.  Errors: PC_EINVAL (NULL). */
+int pc_set_warm_start(pc_ctx* ctx, int on);
+
+/* Sets the start block of the next pc_bands from host memory (count = nk x block x 3N complex
+ * values as 2 count doubles, the layout of pc_export(PC_EXPORT_BLOCK), e.g. from another context
+ * with the same lattice, cutoff, bands and k-points), as a warm start for that call whatever
+ * pc_set_warm_start says (synchronous).  Errors: PC_EINVAL (NULL, wrong count), PC_ESTATE (no
+ * k-points), PC_ECUDA. */
+int pc_import_block(pc_ctx* ctx, const double* host, long long count);
 
 /* Applies the condensed operator and the mass operator at wavevector index k to
  * ncols vectors: x_dev, ax_dev, ox_dev hold ncols x 3N complex (interleaved),

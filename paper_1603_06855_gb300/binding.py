@@ -15,7 +15,9 @@ PC_SC, PC_BCC, PC_FCC = 0, 1, 2
 PC_FP64, PC_MIXED = 0, 1
 PC_GAP_OMEGA, PC_GAP_LAMBDA, PC_GRAD_ALLBANDS = 0, 1, 2
 PC_CLUSTER_TOL_FP64, PC_CLUSTER_TOL_MIXED = 1e-8, 1e-6
-PC_EXPORT_SFAC, PC_EXPORT_TOEP, PC_EXPORT_WINV, PC_EXPORT_EIGVEC, PC_EXPORT_LAMBDA, PC_EXPORT_WEIGHT = range(6)
+PC_EXPORT_SFAC, PC_EXPORT_TOEP, PC_EXPORT_WINV, PC_EXPORT_EIGVEC, PC_EXPORT_LAMBDA, PC_EXPORT_WEIGHT, PC_EXPORT_BLOCK = range(7)
+PC_LAW_COMPLIANCE, PC_LAW_YOUNG = 0, 1
+LAWS = {"compliance": PC_LAW_COMPLIANCE, "young": PC_LAW_YOUNG}
 LATTICES = {"sc": PC_SC, "bcc": PC_BCC, "fcc": PC_FCC}
 
 
@@ -36,6 +38,7 @@ class pc_params(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("tol", ctypes.c_double),
         ("max_iter", ctypes.c_int),
+        ("law", ctypes.c_int),
     ]
 
 
@@ -85,7 +88,8 @@ EXPORTED = ["pc_create", "pc_set_kpoints", "pc_set_design", "pc_bands", "pc_gap_
             "pc_get_stats",
             "pc_clear_status", "pc_set_profiling", "pc_probe", "pc_destroy", "pc_strerror", "pc_export",
             "pc_apply_operator", "pc_check_tensor_kernels", "pc_structure_factors_noalloc", "pc_mma_step",
-            "pc_design_create", "pc_design_nvars", "pc_design_project", "pc_design_backprop", "pc_design_destroy"]
+            "pc_design_create", "pc_design_nvars", "pc_design_project", "pc_design_backprop", "pc_design_destroy",
+            "pc_set_warm_start", "pc_import_block"]
 
 _lib = None
 
@@ -123,6 +127,8 @@ def load(path: str = LIB_PATH):
     lib.pc_design_project.argtypes = [P, P, D, P, P]
     lib.pc_design_backprop.argtypes = [P, P, P, P]
     lib.pc_design_destroy.argtypes = [P]
+    lib.pc_set_warm_start.argtypes = [P, I]
+    lib.pc_import_block.argtypes = [P, P, LL]
     for name in EXPORTED:
         if name not in ("pc_destroy", "pc_strerror", "pc_design_destroy", "pc_design_nvars"):
             getattr(lib, name).restype = I
@@ -148,7 +154,7 @@ def _check(rc: int, where: str):
 
 
 def make_params(lattice, n, M, nbands, phase1, phase0, penal=1.0, precision=PC_FP64, a=1.0, tol=0.0,
-                max_iter=0) -> pc_params:
+                max_iter=0, law=PC_LAW_COMPLIANCE) -> pc_params:
     p = pc_params()
     p.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
     p.a = float(a)
@@ -162,6 +168,7 @@ def make_params(lattice, n, M, nbands, phase1, phase0, penal=1.0, precision=PC_F
     p.precision = int(precision)
     p.tol = float(tol)
     p.max_iter = int(max_iter)
+    p.law = LAWS[law] if isinstance(law, str) else int(law)
     return p
 
 
@@ -294,3 +301,13 @@ def pc_design_backprop(d: int, g_rho_ptr: int, g_x_ptr: int, stream: int = 0) ->
 def pc_design_destroy(d: int) -> None:
     if d:
         load().pc_design_destroy(d)
+
+
+def pc_set_warm_start(ctx: int, on: bool) -> None:
+    _check(load().pc_set_warm_start(ctx, 1 if on else 0), "pc_set_warm_start")
+
+
+def pc_import_block(ctx: int, block) -> None:
+    import numpy as np
+    b = np.ascontiguousarray(block, dtype=np.float64)
+    _check(load().pc_import_block(ctx, b.ctypes.data, b.size // 2), "pc_import_block")

@@ -2,7 +2,9 @@
 // and the adjoint design sensitivities (Methods, eqs. normalev, sensitivityew, diffOmega,
 // diffPhi).  With theta^H Omega theta = 1 and s = Phi^-1 H^H theta,
 //   d lambda / d rho_e = chi'_e v_e [ -lambda (rho1 - rho0) sum_c |u_c(x_e)|^2
-//                                      - (f1_1 - f1_0) |sigma_bulk(x_e)|^2 - (f2_1 - f2_0) |sigma_dev(x_e)|^2 ],
+//                                      - f1'_e |sigma_bulk(x_e)|^2 - f2'_e |sigma_dev(x_e)|^2 ],
+// f1'_e, f2'_e the derivatives of the compliance moduli with respect to chi at element e (the
+// phase differences under the compliance law, per element under eq. combinematerial's law),
 // where u and sigma are the displacement and stress fields synthesised at the element
 // centroid from the plane-wave coefficients.  The kernels synthesise the 3 + 6 fields of
 // every weighted (k, band) on the voxel grid by separable sums (axis 2, axis 1 into a
@@ -272,7 +274,8 @@ __global__ void k_adj_reduce(AdjointArgs a) {
   const long long fstride = (long long)M2 * n1 * n2;
   const long long gstride = (long long)n1 * n2;
   const C2* t2 = (const C2*)a.t2;
-  double acc = 0.0;
+  // the compliance part's factors d f1/d chi, d f2/d chi belong to the element: three weighted sums
+  double acc_m = 0.0, acc_1 = 0.0, acc_2 = 0.0;
   for (int p = 0; p < np; ++p) {
     const int pr = a.pairs[p];
     const double w = a.weights[pr];
@@ -289,9 +292,13 @@ __global__ void k_adj_reduce(AdjointArgs a) {
     }
     double u2 = (double)q[0] + q[1] + q[2];
     double sd = (double)q[4] + q[5] + q[6] + q[7] + q[8];
-    acc += w * (-lam * a.d_rho * u2 - a.two_pi_V_sq * (a.d_f1 * (double)q[3] + a.d_f2 * sd));
+    acc_m += w * lam * u2;
+    acc_1 += w * (double)q[3];
+    acc_2 += w * sd;
   }
   const long long e = ((long long)i * n1 + j) * n2 + l;
+  const long long ne = (long long)n0 * n1 * n2;
+  const double acc = -a.d_rho * acc_m - a.two_pi_V_sq * (a.dfc[e] * acc_1 + a.dfc[ne + e] * acc_2);
   a.grad[e] = acc * a.inv_sO * a.ve * a.dchi[e];
 }
 

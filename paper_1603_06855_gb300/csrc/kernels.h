@@ -6,6 +6,8 @@
 bool pc_material_ok(const pc_material& m);
 
 struct MaterialConsts {
+  int law;             // PC_LAW_COMPLIANCE | PC_LAW_YOUNG
+  double E0, E1, nu0, nu1;  // Young's modulus and Poisson ratio of phase0 / phase1 (PC_LAW_YOUNG)
   double penal;
   double rho0, rho1;   // mass density of phase0 / phase1
   double f1_0, f1_1;   // bulk compliance (1-2nu)/E
@@ -20,6 +22,7 @@ struct SetupArgs {
   double* fields;   // 3 x ne
   double* dchi;     // ne
   double* chi;      // ne
+  double* dfc;      // 2 x ne: d f1 / d chi, d f2 / d chi per element
   double* chi_mean; // 1
   double2* t1;      // 3 x n0 x n1 x L
   double2* t2;      // 3 x n0 x L x L
@@ -161,7 +164,8 @@ struct AdjointArgs {
   int nk, nb, m, N, M, n0, n1, n2;
   double lref;           // physical lambda scale
   double inv_sO;         // |theta_phys|^2 = |X'|^2 / sO
-  double d_rho, d_f1, d_f2;
+  double d_rho;
+  const double* dfc;     // 2 x ne: d f1 / d chi and d f2 / d chi per element
   double two_pi_V_sq;    // (2 pi V)^2
   double ve;             // element volume
   const double* dchi;

@@ -20,7 +20,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[PC_NOALLOC_BYTE
 
 // Kernels of the structure-factor step (defined in setup.cu).
 __global__ void k_interp(const double* __restrict__ rho, int ne, MaterialConsts mc, double* __restrict__ fields,
-                         double* __restrict__ dchi, double* __restrict__ chi_out, int* status);
+                         double* __restrict__ dchi, double* __restrict__ chi_out, int* status, double* dfc);
 __global__ void k_sfac1(const double* __restrict__ fields, int n0, int n1, int n2, int M, double2* __restrict__ t1);
 __global__ void k_sfac2(const double2* __restrict__ t1, int n0, int n1, int M, double2* __restrict__ t2);
 __global__ void k_sfac3(const double2* __restrict__ t2, int n0, int M, double inv_ne, double2* __restrict__ sf);
@@ -61,6 +61,7 @@ extern "C" int pc_structure_factors_noalloc(const pc_params* p, const double* rh
     if (p->n[i] < 1 || p->n[i] > 256) return PC_EINVAL;
   if (!pc_material_ok(p->phase0) || !pc_material_ok(p->phase1)) return PC_EINVAL;
   if (!(p->penal >= 1.0) || !std::isfinite(p->penal)) return PC_EINVAL;
+  if (p->law != PC_LAW_COMPLIANCE && p->law != PC_LAW_YOUNG) return PC_EINVAL;
   const int M2 = 2 * p->M + 1;
   for (int i = 0; i < 3; ++i)
     if (p->n[i] < M2) return PC_EALIAS;
@@ -87,6 +88,11 @@ extern "C" int pc_structure_factors_noalloc(const pc_params* p, const double* rh
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
   MaterialConsts mc;
+  mc.law = p->law;
+  mc.E0 = p->phase0.E;
+  mc.E1 = p->phase1.E;
+  mc.nu0 = p->phase0.nu;
+  mc.nu1 = p->phase1.nu;
   mc.penal = p->penal;
   mc.rho0 = p->phase0.rho;
   mc.rho1 = p->phase1.rho;
@@ -96,7 +102,7 @@ extern "C" int pc_structure_factors_noalloc(const pc_params* p, const double* rh
   mc.f2_1 = (1.0 + p->phase1.nu) / p->phase1.E;
   // the status word is the only part read before written: clear it for this call
   PC_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
-  k_interp<<<cdiv(ne, 256), 256, 0, s>>>(rho_dev, (int)ne, mc, fields, dchi, chi, status);
+  k_interp<<<cdiv(ne, 256), 256, 0, s>>>(rho_dev, (int)ne, mc, fields, dchi, chi, status, nullptr);
   PC_LAUNCH_CHECK();
   const long long t1n = 3LL * n0 * n1 * L;
   k_sfac1<<<cdiv(t1n, 256), 256, 0, s>>>(fields, n0, n1, n2, p->M, t1);

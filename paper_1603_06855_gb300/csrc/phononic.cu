@@ -50,6 +50,9 @@ struct pc_ctx {
   MaterialConsts mc;
   PrecRef pr;
   bool have_design = false, have_bands = false, have_grad = false;
+  int warm = 0;                  // pc_set_warm_start: start from the last final Ritz block
+  bool warm_ready = false;       // Th holds a final block of the current k-points
+  bool import_pending = false;   // pc_import_block: use Th as the start block of the next pc_bands
   int iterations = 0, unconv = 0;
   double max_res = 0.0;
   float ms_setup = 0.f, ms_bands = 0.f, ms_grad = 0.f;
@@ -59,7 +62,7 @@ struct pc_ctx {
   bool have_grad_events = false;
   int* h_unconv = nullptr;  // pinned
   // per-design (FP64)
-  double *fields = nullptr, *dchi = nullptr, *chi = nullptr, *chi_mean = nullptr;
+  double *fields = nullptr, *dchi = nullptr, *chi = nullptr, *chi_mean = nullptr, *dfc = nullptr;
   double2 *t1 = nullptr, *t2s = nullptr, *sfac = nullptr, *T = nullptr, *W = nullptr, *gj_row = nullptr, *gj_col = nullptr;
   float2 *Wf = nullptr, *Tf = nullptr;  // scaled FP32 copies (mixed path)
   int* status = nullptr;
@@ -237,12 +240,14 @@ static void free_kset(pc_ctx* c) {
   c->nk = 0;
   c->have_bands = false;
   c->have_grad = false;
+  c->warm_ready = false;
+  c->import_pending = false;
 }
 
 extern "C" void pc_destroy(pc_ctx* c) {
   if (!c) return;
   free_kset(c);
-  dfree(c->fields); dfree(c->dchi); dfree(c->chi); dfree(c->chi_mean);
+  dfree(c->fields); dfree(c->dchi); dfree(c->chi); dfree(c->chi_mean); dfree(c->dfc);
   dfree(c->t1); dfree(c->t2s); dfree(c->sfac); dfree(c->T); dfree(c->W); dfree(c->gj_row); dfree(c->gj_col);
   dfree(c->Wf); dfree(c->Tf); dfree(c->status); dfree(c->small_flops);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -273,6 +278,7 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
   if (!(p->penal >= 1.0) || !std::isfinite(p->penal)) return PC_EINVAL;
   if (p->precision != PC_FP64 && p->precision != PC_MIXED) return PC_EINVAL;
   if (p->tol < 0 || p->max_iter < 0) return PC_EINVAL;
+  if (p->law != PC_LAW_COMPLIANCE && p->law != PC_LAW_YOUNG) return PC_EINVAL;
   const int M2 = 2 * p->M + 1;
   const int N = M2 * M2 * M2;
   if (p->nbands < 1 || p->nbands > 24 || p->nbands > N) return PC_EINVAL;
@@ -324,6 +330,11 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
   memcpy(c->geom.T, c->Tm, sizeof(c->Tm));
   c->geom.M = p->M;
   c->geom.N = N;
+  c->mc.law = p->law;
+  c->mc.E0 = p->phase0.E;
+  c->mc.E1 = p->phase1.E;
+  c->mc.nu0 = p->phase0.nu;
+  c->mc.nu1 = p->phase1.nu;
   c->mc.penal = p->penal;
   c->mc.rho0 = p->phase0.rho;
   c->mc.rho1 = p->phase1.rho;
@@ -364,6 +375,7 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
   rc |= dalloc(&c->fields, 3 * ne);
   rc |= dalloc(&c->dchi, ne);
   rc |= dalloc(&c->chi, ne);
+  rc |= dalloc(&c->dfc, 2 * ne);
   rc |= dalloc(&c->chi_mean, 1);
   rc |= dalloc(&c->t1, 3 * (size_t)p->n[0] * p->n[1] * L);
   rc |= dalloc(&c->t2s, 3 * (size_t)p->n[0] * L * L);
@@ -477,7 +489,7 @@ extern "C" int pc_set_design(pc_ctx* c, const double* rho, void* stream) {
   a.M = c->prm.M;
   a.V = c->V;
   a.mc = c->mc;
-  a.fields = c->fields; a.dchi = c->dchi; a.chi = c->chi; a.chi_mean = c->chi_mean;
+  a.fields = c->fields; a.dchi = c->dchi; a.chi = c->chi; a.chi_mean = c->chi_mean; a.dfc = c->dfc;
   a.t1 = c->t1; a.t2 = c->t2s; a.sfac = c->sfac; a.T = c->T; a.W = c->W;
   a.gj_row = c->gj_row; a.gj_col = c->gj_col;
   a.status = c->status;
@@ -701,7 +713,18 @@ static int run_block_iteration(pc_ctx* c, KSet& ks) {
   PC_CUDA_TRY(cudaMemsetAsync(kdone, 0, sizeof(int) * nk, s));
   PC_CUDA_TRY(cudaMemsetAsync(sbest, 0, sizeof(double) * nk, s));
   PC_CUDA_TRY(cudaMemsetAsync(ssince, 0, sizeof(int) * nk, s));
-  TRY(launch_init_guess<R>(X, nk, m, c->geom, Qk, c->seed, s));
+  if (c->import_pending || (c->warm && c->warm_ready)) {
+    // warm start: the final Ritz block of the last pc_bands (or the imported one), FP64 in Th
+    const double2* th = c->Th + (long long)k0 * m * n3;
+    const long long cnt = (long long)nk * m * n3;
+    if constexpr (std::is_same<R, float>::value) {
+      TRY(launch_d2f(th, (float2*)X, cnt, 1.0, s));
+    } else {
+      PC_CUDA_TRY(cudaMemcpyAsync(X, th, sizeof(double2) * cnt, cudaMemcpyDeviceToDevice, s));
+    }
+  } else {
+    TRY(launch_init_guess<R>(X, nk, m, c->geom, Qk, c->seed, s));
+  }
   TRY(apply_R<R>(c, ks, X, AX, OX));
   {
     BlockList<R> A1 = {{X, nullptr, nullptr}}, B1 = {{AX, nullptr, nullptr}}, B2 = {{OX, nullptr, nullptr}};
@@ -982,6 +1005,8 @@ extern "C" int pc_bands(pc_ctx* c, double* omega, void* stream) {
   if (rc) return rc;
   PC_CUDA_TRY(cudaEventRecord(c->ev1, s));
   c->have_bands = true;
+  c->warm_ready = true;
+  c->import_pending = false;
   c->have_grad = false;
   return PC_OK;
 }
@@ -1024,8 +1049,7 @@ static int gap_and_grad_impl(pc_ctx* c, int n_lower, int mode, double beta, cons
     a.lref = c->lref;
     a.inv_sO = 1.0 / c->sO;
     a.d_rho = c->mc.rho1 - c->mc.rho0;
-    a.d_f1 = c->mc.f1_1 - c->mc.f1_0;
-    a.d_f2 = c->mc.f2_1 - c->mc.f2_0;
+    a.dfc = c->dfc;
     a.two_pi_V_sq = (2.0 * M_PI * c->V) * (2.0 * M_PI * c->V);
     a.ve = c->ve;
     a.dchi = c->dchi;
@@ -1192,6 +1216,7 @@ extern "C" int pc_export(pc_ctx* c, int which, double* host, long long cap, long
     case PC_EXPORT_LAMBDA: if (!c->have_bands) return PC_ESTATE; n = (long long)c->nk * c->nb; break;
     case PC_EXPORT_EIGVEC: if (!c->have_bands) return PC_ESTATE; n = (long long)c->nk * c->nb * 3 * N * 2; break;
     case PC_EXPORT_WEIGHT: if (!c->have_grad) return PC_ESTATE; src = c->weights; n = (long long)c->nk * c->nb; break;
+    case PC_EXPORT_BLOCK: if (!c->warm_ready) return PC_ESTATE; src = c->Th; n = (long long)c->nk * c->m * 3 * N * 2; break;
     default: return PC_EINVAL;
   }
   *count = n;
@@ -1213,6 +1238,22 @@ extern "C" int pc_export(pc_ctx* c, int which, double* host, long long cap, long
     return PC_OK;
   }
   PC_CUDA_TRY(cudaMemcpy(host, src, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  return PC_OK;
+}
+
+extern "C" int pc_set_warm_start(pc_ctx* c, int on) {
+  if (!c) return PC_EINVAL;
+  c->warm = on ? 1 : 0;
+  return PC_OK;
+}
+
+extern "C" int pc_import_block(pc_ctx* c, const double* host, long long count) {
+  if (!c || !host) return PC_EINVAL;
+  if (c->nk == 0) return PC_ESTATE;
+  if (count != (long long)c->nk * c->m * 3 * c->N) return PC_EINVAL;
+  PC_CUDA_TRY(cudaDeviceSynchronize());
+  PC_CUDA_TRY(cudaMemcpy(c->Th, host, sizeof(double2) * count, cudaMemcpyHostToDevice));
+  c->import_pending = true;
   return PC_OK;
 }
 

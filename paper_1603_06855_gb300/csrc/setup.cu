@@ -10,10 +10,13 @@
 #include "kernels.h"
 
 // ---------------------------------------------------------------------------
-// SIMP interpolation: fields[0] = density, fields[1] = f1, fields[2] = f2 per element.
+// SIMP interpolation: fields[0] = density, fields[1] = f1, fields[2] = f2 per element, and
+// dfc = (d f1 / d chi, d f2 / d chi) per element (dfc may be NULL).  PC_LAW_COMPLIANCE: f1, f2
+// linear in chi; PC_LAW_YOUNG: E and nu linear in chi, f1 = (1 - 2 nu)/E, f2 = (1 + nu)/E, so
+// d f1/d chi = (-2 dnu E - (1 - 2 nu) dE) / E^2 and d f2/d chi = (dnu E - (1 + nu) dE) / E^2.
 __global__ void k_interp(const double* __restrict__ rho, int ne, MaterialConsts mc,
                          double* __restrict__ fields, double* __restrict__ dchi,
-                         double* __restrict__ chi_out, int* status) {
+                         double* __restrict__ chi_out, int* status, double* __restrict__ dfc) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
   double r = rho[e];
@@ -26,8 +29,26 @@ __global__ void k_interp(const double* __restrict__ rho, int ne, MaterialConsts 
   if (mc.penal == 1.0) { chi = r; dc = 1.0; }
   else { chi = pow(r, mc.penal); dc = (r > 0.0) ? mc.penal * pow(r, mc.penal - 1.0) : 0.0; }
   fields[e] = mc.rho0 + chi * (mc.rho1 - mc.rho0);
-  fields[ne + e] = mc.f1_0 + chi * (mc.f1_1 - mc.f1_0);
-  fields[2 * ne + e] = mc.f2_0 + chi * (mc.f2_1 - mc.f2_0);
+  double f1, f2, d1, d2;
+  if (mc.law == PC_LAW_YOUNG) {
+    const double dE = mc.E1 - mc.E0, dn = mc.nu1 - mc.nu0;
+    const double E = mc.E0 + chi * dE, nu = mc.nu0 + chi * dn;
+    f1 = (1.0 - 2.0 * nu) / E;
+    f2 = (1.0 + nu) / E;
+    d1 = (-2.0 * dn * E - (1.0 - 2.0 * nu) * dE) / (E * E);
+    d2 = (dn * E - (1.0 + nu) * dE) / (E * E);
+  } else {
+    f1 = mc.f1_0 + chi * (mc.f1_1 - mc.f1_0);
+    f2 = mc.f2_0 + chi * (mc.f2_1 - mc.f2_0);
+    d1 = mc.f1_1 - mc.f1_0;
+    d2 = mc.f2_1 - mc.f2_0;
+  }
+  fields[ne + e] = f1;
+  fields[2 * ne + e] = f2;
+  if (dfc) {
+    dfc[e] = d1;
+    dfc[ne + e] = d2;
+  }
   dchi[e] = dc;
   chi_out[e] = chi;
 }
@@ -223,7 +244,7 @@ int launch_setup(const SetupArgs& a, cudaStream_t s) {
   const int ne = a.n0 * a.n1 * a.n2;
   const int L = 4 * a.M + 1;
   const int N = (2 * a.M + 1) * (2 * a.M + 1) * (2 * a.M + 1);
-  k_interp<<<cdiv(ne, 256), 256, 0, s>>>(a.rho, ne, a.mc, a.fields, a.dchi, a.chi, a.status);
+  k_interp<<<cdiv(ne, 256), 256, 0, s>>>(a.rho, ne, a.mc, a.fields, a.dchi, a.chi, a.status, a.dfc);
   PC_LAUNCH_CHECK();
   k_mean<<<1, 1024, 0, s>>>(a.chi, ne, a.chi_mean);
   PC_LAUNCH_CHECK();

@@ -13,13 +13,13 @@ class BandSolver:
     """One design context: lattice, grid, cutoff, bands, precision and a k-point set."""
 
     def __init__(self, lattice, n, M, nbands, phase1, phase0, Q, penal=1.0, precision=B.PC_FP64, a=1.0,
-                 tol=0.0, max_iter=0, device="cuda"):
+                 tol=0.0, max_iter=0, device="cuda", law="compliance"):
         if isinstance(precision, str):
             precision = {"fp64": B.PC_FP64, "mixed": B.PC_MIXED}[precision]
         self.device = torch.device(device)
         self.n = tuple(int(x) for x in n)
         self.nbands = int(nbands)
-        self.params = B.make_params(lattice, n, M, nbands, phase1, phase0, penal, precision, a, tol, max_iter)
+        self.params = B.make_params(lattice, n, M, nbands, phase1, phase0, penal, precision, a, tol, max_iter, law)
         self.ctx = B.pc_create(self.params)
         self.Q = np.ascontiguousarray(Q, dtype=np.float64)
         B.pc_set_kpoints(self.ctx, self.Q)
@@ -78,6 +78,14 @@ class BandSolver:
 
     def export(self, which: int) -> np.ndarray:
         return B.pc_export(self.ctx, which)
+
+    def set_warm_start(self, on: bool = True) -> None:
+        """Start each bands() from the previous call's final Ritz block (same k-points)."""
+        B.pc_set_warm_start(self.ctx, on)
+
+    def import_block(self, block: np.ndarray) -> None:
+        """Start the next bands() from a block exported by export(PC_EXPORT_BLOCK)."""
+        B.pc_import_block(self.ctx, block)
 
     def stats(self):
         return B.pc_get_stats(self.ctx)

@@ -45,7 +45,7 @@ def _params(**kw):
     (dict(M=0), 1), (dict(M=6), 1), (dict(nbands=0), 1), (dict(nbands=25), 1), (dict(lattice=7), 1),
     (dict(n=(8, 0, 8)), 1), (dict(penal=0.5), 1), (dict(precision=3), 1), (dict(a=-1.0), 1),
     (dict(phase1=dict(rho=1.0, E=1.0, nu=0.5)), 1), (dict(phase0=dict(rho=-1.0, E=1.0, nu=0.3)), 1),
-    (dict(n=(8, 4, 8), M=2), 2), (dict(n=(2, 8, 8), M=1), 2),
+    (dict(n=(8, 4, 8), M=2), 2), (dict(n=(2, 8, 8), M=1), 2), (dict(law=2), 1), (dict(law=-1), 1),
 ])
 def test_create_rejects_bad_parameters(kw, code):
     B = _lib()
@@ -59,6 +59,8 @@ def test_null_handles_rejected():
     assert lib.pc_bands(None, None, None) == B.PC_EINVAL
     assert lib.pc_gap_and_grad(None, 1, 0, None, None, None, None) == B.PC_EINVAL
     assert lib.pc_clear_status(None) == B.PC_EINVAL
+    assert lib.pc_set_warm_start(None, 1) == B.PC_EINVAL
+    assert lib.pc_import_block(None, None, 0) == B.PC_EINVAL
     lib.pc_destroy(None)
 
 
@@ -102,7 +104,7 @@ def test_mma_step_rejects_bad_arguments():
     (dict(phase1=dict(rho=1.0, E=1.0, nu=0.5)), 1), (dict(phase0=dict(rho=1.0, E=float("nan"), nu=0.3)), 1),
     (dict(phase0=dict(rho=float("inf"), E=1.0, nu=0.3)), 1), (dict(phase1=dict(rho=1.0, E=1.0, nu=-1.0)), 1),
     (dict(penal=float("inf")), 1), (dict(penal=0.5), 1), (dict(M=0), 1), (dict(M=6), 1),
-    (dict(n=(300, 8, 8)), 1), (dict(n=(8, 0, 8)), 1),
+    (dict(n=(300, 8, 8)), 1), (dict(n=(8, 0, 8)), 1), (dict(law=3), 1),
     (dict(n=(8, 4, 8), M=2), 2),
     (dict(n=(48, 48, 48), M=2), 9), (dict(n=(64, 64, 64)), 9),
 ])
