@@ -267,6 +267,41 @@ int pc_design_backprop(pc_design* d, const double* g_rho_dev, double* g_x_dev, v
 /* Frees the map.  NULL is allowed. */
 void pc_design_destroy(pc_design* d);
 
+/* --- Batches of designs of different lattices, grids and cutoffs (Methods, "Vectorization and
+ * parallel computations": all wavevectors solved together) ---
+ *
+ * One handle over ndesigns designs, each with its own pc_params and k-points.  Every call below
+ * enqueues the work of every design: a pool of `workers` host threads, each with its own
+ * non-blocking stream forked from the caller's stream, drains a queue of the designs ordered by
+ * estimated work (k-points x N^2, FP64 designs weighted 60x), largest first; the streams are joined
+ * back to the caller's stream before the call returns, so the results are stream ordered like the
+ * single-design calls.  Packed layouts, designs in order: rho and grad hold n0 n1 n2 doubles per
+ * design, omega and w nk x nbands per design, gap one double per design.
+ * kgroups: concurrent k groups inside each mixed-form design (0: the context default).
+ * Errors of the per-design calls are returned (the first one); pc_batch_get_stats reads a design's
+ * status. */
+typedef struct pc_batch pc_batch;
+
+/* params: ndesigns parameter sets; q_host: the reduced k-points of every design, concatenated
+ * (nk[d] rows of 3 doubles each); workers in 1..16 (at most ndesigns are used); kgroups in 0..6.
+ * Errors: PC_EINVAL (NULL, counts, any design's parameters), PC_EALIAS, PC_ENOMEM, PC_ECUDA. */
+int pc_batch_create(const pc_params* params, int ndesigns, const double* q_host, const int* nk, int workers,
+                    int kgroups, pc_batch** out);
+/* pc_set_design of every design (rho_dev packed).  Errors: PC_EINVAL, PC_ECUDA. */
+int pc_batch_set_designs(pc_batch* b, const double* rho_dev, void* stream);
+/* pc_bands of every design (omega_dev packed).  Errors: PC_EINVAL, PC_ESTATE, PC_ECUDA. */
+int pc_batch_bands(pc_batch* b, double* omega_dev, void* stream);
+/* pc_gap_and_grad of every design: n_lower_host one value per design (ignored for
+ * PC_GRAD_ALLBANDS), w_dev packed weights for PC_GRAD_ALLBANDS, gap_dev ndesigns doubles,
+ * grad_dev packed or NULL.  Errors: PC_EINVAL (checked for every design before anything is
+ * enqueued), PC_ESTATE, PC_ECUDA. */
+int pc_batch_gap_and_grad(pc_batch* b, const int* n_lower_host, int mode, const double* w_dev, double* gap_dev,
+                          double* grad_dev, void* stream);
+/* pc_get_stats of one design.  Errors: PC_EINVAL (design out of range) or the design's status. */
+int pc_batch_get_stats(pc_batch* b, int design, pc_stats* out);
+/* Frees every design's context and the workers' streams.  NULL is allowed. */
+void pc_batch_destroy(pc_batch* b);
+
 /* Synchronises the device and fills *out; returns out->status as well. */
 int pc_get_stats(pc_ctx* ctx, pc_stats* out);
 

@@ -89,7 +89,8 @@ EXPORTED = ["pc_create", "pc_set_kpoints", "pc_set_design", "pc_bands", "pc_gap_
             "pc_clear_status", "pc_set_profiling", "pc_probe", "pc_destroy", "pc_strerror", "pc_export",
             "pc_apply_operator", "pc_check_tensor_kernels", "pc_structure_factors_noalloc", "pc_mma_step",
             "pc_design_create", "pc_design_nvars", "pc_design_project", "pc_design_backprop", "pc_design_destroy",
-            "pc_set_warm_start", "pc_import_block"]
+            "pc_set_warm_start", "pc_import_block", "pc_batch_create", "pc_batch_set_designs", "pc_batch_bands",
+            "pc_batch_gap_and_grad", "pc_batch_get_stats", "pc_batch_destroy"]
 
 _lib = None
 
@@ -128,12 +129,19 @@ def load(path: str = LIB_PATH):
     lib.pc_design_backprop.argtypes = [P, P, P, P]
     lib.pc_design_destroy.argtypes = [P]
     lib.pc_set_warm_start.argtypes = [P, I]
+    lib.pc_batch_create.argtypes = [P, I, P, P, I, I, ctypes.POINTER(P)]
+    lib.pc_batch_set_designs.argtypes = [P, P, P]
+    lib.pc_batch_bands.argtypes = [P, P, P]
+    lib.pc_batch_gap_and_grad.argtypes = [P, P, I, P, P, P, P]
+    lib.pc_batch_get_stats.argtypes = [P, I, ctypes.POINTER(pc_stats)]
+    lib.pc_batch_destroy.argtypes = [P]
     lib.pc_import_block.argtypes = [P, P, LL]
     for name in EXPORTED:
-        if name not in ("pc_destroy", "pc_strerror", "pc_design_destroy", "pc_design_nvars"):
+        if name not in ("pc_destroy", "pc_strerror", "pc_design_destroy", "pc_design_nvars", "pc_batch_destroy"):
             getattr(lib, name).restype = I
     lib.pc_design_nvars.restype = LL
     lib.pc_design_destroy.restype = None
+    lib.pc_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -311,3 +319,47 @@ def pc_import_block(ctx: int, block) -> None:
     import numpy as np
     b = np.ascontiguousarray(block, dtype=np.float64)
     _check(load().pc_import_block(ctx, b.ctypes.data, b.size // 2), "pc_import_block")
+
+
+def pc_batch_create_rc(params, q_host, nk, workers: int = 1, kgroups: int = 0):
+    """(return code, handle or 0) for a list of pc_params, concatenated k-points and counts."""
+    import numpy as np
+    arr = (pc_params * len(params))(*params)
+    q = np.ascontiguousarray(q_host, dtype=np.float64)
+    counts = np.ascontiguousarray(nk, dtype=np.int32)
+    h = ctypes.c_void_p()
+    rc = load().pc_batch_create(ctypes.addressof(arr), len(params), q.ctypes.data, counts.ctypes.data, int(workers),
+                                int(kgroups), ctypes.byref(h))
+    return rc, (h.value or 0)
+
+
+def pc_batch_create(params, q_host, nk, workers: int = 1, kgroups: int = 0) -> int:
+    rc, h = pc_batch_create_rc(params, q_host, nk, workers, kgroups)
+    _check(rc, "pc_batch_create")
+    return h
+
+
+def pc_batch_set_designs(b: int, rho_ptr: int, stream: int = 0) -> None:
+    _check(load().pc_batch_set_designs(b, rho_ptr, stream), "pc_batch_set_designs")
+
+
+def pc_batch_bands(b: int, omega_ptr: int, stream: int = 0) -> None:
+    _check(load().pc_batch_bands(b, omega_ptr, stream), "pc_batch_bands")
+
+
+def pc_batch_gap_and_grad(b: int, n_lower, mode: int, w_ptr: int, gap_ptr: int, grad_ptr: int, stream: int = 0):
+    import numpy as np
+    nl = np.ascontiguousarray(n_lower, dtype=np.int32)
+    _check(load().pc_batch_gap_and_grad(b, nl.ctypes.data, mode, w_ptr, gap_ptr, grad_ptr, stream),
+           "pc_batch_gap_and_grad")
+
+
+def pc_batch_get_stats(b: int, design: int) -> pc_stats:
+    st = pc_stats()
+    load().pc_batch_get_stats(b, design, ctypes.byref(st))
+    return st
+
+
+def pc_batch_destroy(b: int) -> None:
+    if b:
+        load().pc_batch_destroy(b)

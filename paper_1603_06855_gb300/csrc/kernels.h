@@ -4,6 +4,8 @@
 
 // A phase accepted by pc_create: rho > 0, E > 0 (both finite), -1 < nu < 0.5.
 bool pc_material_ok(const pc_material& m);
+// Concurrent k groups of a context's mixed form, set before pc_set_kpoints (phononic.cu).
+int pc_internal_set_groups(pc_ctx* c, int groups);
 
 struct MaterialConsts {
   int law;             // PC_LAW_COMPLIANCE | PC_LAW_YOUNG

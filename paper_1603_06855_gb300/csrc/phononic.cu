@@ -1241,6 +1241,14 @@ extern "C" int pc_export(pc_ctx* c, int which, double* host, long long cap, long
   return PC_OK;
 }
 
+// Concurrent k groups of the mixed form for the next pc_set_kpoints (batch contexts; 1: one
+// stream).  Not exported.
+int pc_internal_set_groups(pc_ctx* c, int groups) {
+  if (!c || groups < 1 || groups > kMaxGroups) return PC_EINVAL;
+  c->groups = groups;
+  return PC_OK;
+}
+
 extern "C" int pc_set_warm_start(pc_ctx* c, int on) {
   if (!c) return PC_EINVAL;
   c->warm = on ? 1 : 0;

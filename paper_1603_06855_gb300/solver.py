@@ -253,3 +253,77 @@ def maximize_gap(solver: BandSolver, rho: torch.Tensor, n_lower: int, beta: floa
     g, _ = evaluate(steps, False)
     history.append(float(g.item()))
     return (x.view(solver.n) if design is None else x), history
+
+
+class BatchSolver:
+    """Designs of different lattices, grids, cutoffs and k-points evaluated in one call each
+    (pc_batch_*).  `designs`: objects with lattice, n, M, nbands, phase1, phase0, Q, penal and a
+    (e.g. workloads.Workload).  workers / kgroups: concurrency of the batch (see autotune); the
+    packed outputs are returned as per-design views."""
+
+    def __init__(self, designs, precision=B.PC_MIXED, workers: int = 4, kgroups: int = 0, device="cuda",
+                 law="compliance"):
+        if isinstance(precision, str):
+            precision = {"fp64": B.PC_FP64, "mixed": B.PC_MIXED}[precision]
+        self.device = torch.device(device)
+        self.designs = list(designs)
+        self.params = [B.make_params(w.lattice, w.n, w.M, w.nbands, w.phase1, w.phase0, w.penal, precision,
+                                     getattr(w, "a", 1.0), law=law) for w in self.designs]
+        Q = np.concatenate([np.asarray(w.Q, dtype=np.float64) for w in self.designs], axis=0)
+        self.nk = [int(np.asarray(w.Q).shape[0]) for w in self.designs]
+        self.ne = [int(np.prod(w.n)) for w in self.designs]
+        self.nb = [int(w.nbands) for w in self.designs]
+        self.handle = B.pc_batch_create(self.params, Q, self.nk, workers, kgroups)
+        self.off_rho = np.concatenate([[0], np.cumsum(self.ne)]).astype(int)
+        self.off_om = np.concatenate([[0], np.cumsum([k * b for k, b in zip(self.nk, self.nb)])]).astype(int)
+
+    def _stream(self) -> int:
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def set_designs(self, rhos) -> None:
+        """rhos: one density tensor per design (any shape with n0 n1 n2 values) or a packed tensor."""
+        if isinstance(rhos, torch.Tensor):
+            packed = rhos.detach().to(self.device, torch.float64).contiguous().view(-1)
+        else:
+            packed = torch.cat([torch.as_tensor(r).to(self.device, torch.float64).reshape(-1) for r in rhos])
+        if packed.numel() != self.off_rho[-1]:
+            raise ValueError("densities do not match the designs' grids")
+        self._rho = packed
+        B.pc_batch_set_designs(self.handle, packed.data_ptr(), self._stream())
+
+    def bands(self):
+        om = torch.empty(int(self.off_om[-1]), dtype=torch.float64, device=self.device)
+        B.pc_batch_bands(self.handle, om.data_ptr(), self._stream())
+        self._om = om
+        return [om[self.off_om[d]:self.off_om[d + 1]].view(self.nk[d], self.nb[d]) for d in range(len(self.designs))]
+
+    def gap_and_grad(self, n_lower=None, mode: int = B.PC_GAP_OMEGA, weights=None, need_grad: bool = True):
+        nd = len(self.designs)
+        gap = torch.empty(nd, dtype=torch.float64, device=self.device)
+        grad = torch.empty(int(self.off_rho[-1]), dtype=torch.float64, device=self.device) if need_grad else None
+        wptr = 0
+        if weights is not None:
+            wt = torch.cat([torch.as_tensor(w).to(self.device, torch.float64).reshape(-1) for w in weights])
+            self._w = wt
+            wptr = wt.data_ptr()
+        nl = np.ones(nd, dtype=np.int32) if n_lower is None else np.asarray(n_lower, dtype=np.int32)
+        B.pc_batch_gap_and_grad(self.handle, nl, mode, wptr, gap.data_ptr(), grad.data_ptr() if need_grad else 0,
+                                self._stream())
+        grads = None
+        if need_grad:
+            grads = [grad[self.off_rho[d]:self.off_rho[d + 1]].view(self.designs[d].n) for d in range(nd)]
+        return gap, grads
+
+    def stats(self, design: int):
+        return B.pc_batch_get_stats(self.handle, design)
+
+    def close(self):
+        if getattr(self, "handle", 0):
+            B.pc_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -136,3 +136,21 @@ def test_design_create_rejects_bad_parameters(lattice, n, spacing, rad, octant):
     dp.octant = octant
     rc, h = B.pc_design_create_rc(cell, dp)
     assert rc == B.PC_EINVAL and h == 0
+
+
+def test_batch_create_rejects_bad_arguments():
+    """pc_batch_create checks its counts before creating any context, and a design with bad
+    parameters fails in pc_create's own host checks (no device memory is touched)."""
+    import numpy as np
+    B = _lib()
+    good = _params()
+    q = np.zeros((4, 3))
+    for workers, kgroups, nk in ((0, 0, [2, 2]), (17, 0, [2, 2]), (2, 7, [2, 2]), (2, -1, [2, 2]), (2, 0, [0, 4])):
+        rc, h = B.pc_batch_create_rc([good, good], q, nk, workers, kgroups)
+        assert rc == B.PC_EINVAL and h == 0
+    rc, h = B.pc_batch_create_rc([_params(M=0)], q[:2], [2], 1, 0)
+    assert rc == B.PC_EINVAL and h == 0
+    lib = B.load()
+    assert lib.pc_batch_bands(None, None, None) == B.PC_EINVAL
+    assert lib.pc_batch_set_designs(None, None, None) == B.PC_EINVAL
+    lib.pc_batch_destroy(None)

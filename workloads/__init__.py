@@ -272,3 +272,20 @@ def sphere_inclusion(lattice: str, n, vf: float, sub: int = 3) -> np.ndarray:
             dist = np.minimum(dist, np.linalg.norm((s - sh) @ A.T, axis=1))
         inside += dist <= r
     return (inside / sub ** 3).reshape(n)
+
+
+def sphere_scan(vfs=None, n: int = 24, M: int = 3, nk: int = 31, lattices=("sc", "bcc", "fcc")) -> list[Workload]:
+    """The sphere-inclusion volume-fraction scans of the paper's note on normalized band gaps:
+    for each lattice, one tungsten-carbide sphere per primitive cell in epoxy (the paper's
+    constants) at every volume fraction in vfs (default 0.05 to 0.70 in steps of 0.05), n^3 voxels,
+    cutoff M, nk points along the high-symmetry path, 8 bands for gap(6,7)."""
+    if vfs is None:
+        vfs = [round(0.05 * i, 2) for i in range(1, 15)]
+    out = []
+    for lat in lattices:
+        Q = kpath(lat, nk)
+        for vf in vfs:
+            rho = sphere_inclusion(lat, (n, n, n), vf)
+            out.append(Workload(f"{lat}{n}_M{M}_sphere_vf{vf:.2f}", lat, (n, n, n), M, 8, Q, rho, 1.0, (6,), 0,
+                                1.0, dict(PAPER_WC), dict(PAPER_EPOXY)))
+    return out
