@@ -480,11 +480,23 @@ def main():
         if "iteration_operator_apply" in fam:
             f = fam["iteration_operator_apply"]
             f["frac_of_split_bf16_peak"] = f["achieved"] / (peaks["bf16_tflops_sustained"] / 6.0)
-    add("fp64_rayleigh_ritz_gemm", "k_gemm<double>", st_pf.ms_rr_gemm, st_pf.rr_gemm_flops, st_pf.rr_gemm_launches,
-        "alu", fp64_peak / 1e3, "TFLOP/s", "measured FP64 FMA throughput (pc_probe) on this GPU")
+    # final Rayleigh-Ritz operator products: exact 6-bit slice products on the tensor cores (36 bf16
+    # products per FP64-accurate one) where the plan fits, else the FP64 CUDA-core GEMM
+    if st_pf.rr_sliced and peaks.get("bf16_tflops_sustained"):
+        add("fp64_rayleigh_ritz_gemm", "k_oz_gemm", st_pf.ms_rr_gemm, 36.0 * st_pf.rr_gemm_flops,
+            st_pf.rr_gemm_launches, "tensor", peaks["bf16_tflops_sustained"], "TFLOP/s",
+            "MEASURED_PEAKS.json bf16_tflops_sustained")
+        if "fp64_rayleigh_ritz_gemm" in fam:
+            f = fam["fp64_rayleigh_ritz_gemm"]
+            f["fp64_equivalent_tflops"] = f["achieved"] / 36.0
+            f["fp64_equivalent_over_fp64_fma_peak"] = f["achieved"] / 36.0 / (fp64_peak / 1e3)
+    else:
+        add("fp64_rayleigh_ritz_gemm", "k_gemm<double>", st_pf.ms_rr_gemm, st_pf.rr_gemm_flops,
+            st_pf.rr_gemm_launches, "alu", fp64_peak / 1e3, "TFLOP/s",
+            "measured FP64 FMA throughput (pc_probe) on this GPU")
     # projected eigenproblems (Cholesky, reduction, Jacobi sweeps as executed) against FP32 FMA; the
     # family time also holds the small Cholesky-QR and conjugate-direction kernels
-    add("projected_problems", "k_small_rr32", st_pf.ms_small, st_pf.small_flops, 0, "alu", fp32_peak / 1e3,
+    add("projected_problems", "k_small_rr32", st_pf.ms_small, st_pf.small_flops, st_pf.small_calls, "alu", fp32_peak / 1e3,
         "TFLOP/s", "measured FP32 FMA throughput (pc_probe) on this GPU")
     # adjoint synthesis and reduction (FP32 in the mixed form)
     add("adjoint", "k_adj_synth12+k_adj_reduce", st_pf.ms_grad_kernels,

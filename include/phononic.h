@@ -133,6 +133,11 @@ typedef struct {
                               72 ((2M+1)^3 n2 + (2M+1)^2 n1 n2 + (2M+1) n0 n1 n2) */
   double ms_host_idle;     /* stream idle time while the host reads the convergence count of each block
                               iteration and enqueues the next one (profiling; summed over the k groups) */
+  int rr_sliced;           /* 1 when the Rayleigh-Ritz operator products run as exact 6-bit slice products on
+                              the tensor cores (36 bf16 products per FP64-accurate one; mixed form,
+                              N <= 1008), 0 when they run as the FP64 CUDA-core GEMM */
+  long long small_calls;   /* calls timed in ms_small (profiling): the projected eigenproblem kernel and the
+                              small Cholesky factorisations of the orthonormalisation */
 } pc_stats;
 
 /* Creates a context: validates the parameters and allocates every per-design
@@ -374,7 +379,10 @@ int pc_apply_operator(pc_ctx* ctx, int k, int ncols, const double* x_dev,
  * result|.  what = 2 exercises the failure path of the kernels' bounded barrier waits: a
  * one-thread kernel waits on a barrier that nothing completes, with a short limit; *rel_err = 0
  * when it gave up and recorded PC_ETIMEOUT and the device then accepted further work, else 1
- * (the other arguments are ignored).  Not on the hot path; it switches the library's Gram and
+ * (the other arguments are ignored).  what = 3 checks the FP64-accurate products of the mixed
+ * form's final Rayleigh-Ritz step (exact 6-bit slices on the tensor cores) against the FP64
+ * GEMM: n3 is the plane-wave count N (2N at most 2016), nk * m the columns, on seeded complex
+ * data whose operator rows span eight binades.  Not on the hot path; it switches the library's Gram and
  * update kernel path for its own launches, so it must not run concurrently with other calls.
  * Errors: PC_EINVAL (m > 24,
  * nblk > 3, bad what or sizes), PC_ENOMEM, PC_ECUDA, PC_ETIMEOUT (a bounded wait of a

@@ -81,6 +81,8 @@ class pc_stats(ctypes.Structure):
         ("grad_pairs", ctypes.c_longlong),
         ("grad_flops_per_pair", ctypes.c_double),
         ("ms_host_idle", ctypes.c_double),
+        ("rr_sliced", ctypes.c_int),
+        ("small_calls", ctypes.c_longlong),
     ]
 
 
@@ -262,7 +264,8 @@ def pc_apply_operator(ctx: int, k: int, ncols: int, x_ptr: int, ax_ptr: int, ox_
 
 
 def pc_check_tensor_kernels(what: int, nk: int, m: int, nblk: int, n3: int) -> float:
-    """Tensor-core vs CUDA-core Gram (what=0) or basis update (what=1): max relative difference."""
+    """Tensor-core vs CUDA-core Gram (what=0) or basis update (what=1), or the sliced FP64-accurate
+    product vs the FP64 GEMM (what=3, n3 = N, nk * m columns): max relative difference."""
     err = ctypes.c_double(-1.0)
     _check(load().pc_check_tensor_kernels(what, nk, m, nblk, n3, ctypes.byref(err)), "pc_check_tensor_kernels")
     return err.value

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libphononic.so")
-SOURCES = ["setup.cu", "apply.cu", "lobpcg.cu", "adjoint.cu", "gemm_tc.cu", "tall_tc.cu", "small_rr.cu", "phononic.cu", "no_alloc.cu", "mma.cu", "design.cu", "batch.cu"]
+SOURCES = ["setup.cu", "apply.cu", "lobpcg.cu", "adjoint.cu", "gemm_tc.cu", "tall_tc.cu", "small_rr.cu", "phononic.cu", "no_alloc.cu", "mma.cu", "design.cu", "batch.cu", "oz_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

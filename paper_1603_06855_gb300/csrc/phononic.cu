@@ -88,6 +88,9 @@ struct pc_ctx {
   double2* adj_t2 = nullptr;
   TcPlan* tc = nullptr;
   TcPlan* tcg[kMaxGroups] = {};  // workspaces of k groups 1.. (operators shared with tc)
+  OzPlan* oz = nullptr;          // sliced FP64-accurate operators of the final Rayleigh-Ritz step (mixed form)
+  OzPlan* ozg[kMaxGroups] = {};  // right-hand-side workspaces of k groups 1.. (operators shared with oz)
+  bool oz_ready = false;         // oz holds the slices of the current design
   cudaStream_t sk[kMaxGroups] = {};  // non-blocking streams of the k groups
   cudaEvent_t ev_fork = nullptr, ev_join[kMaxGroups] = {};
   int split = 1;                // PC_SPLIT=0: the block iteration of the mixed form on one stream
@@ -237,6 +240,10 @@ static void free_kset(pc_ctx* c) {
   for (auto& t : c->tcg)
     if (t) { tc_plan_destroy(t); t = nullptr; }
   if (c->tc) { tc_plan_destroy(c->tc); c->tc = nullptr; }
+  for (auto& o : c->ozg)
+    if (o) { oz_plan_destroy(o); o = nullptr; }
+  if (c->oz) { oz_plan_destroy(c->oz); c->oz = nullptr; }
+  c->oz_ready = false;
   c->nk = 0;
   c->have_bands = false;
   c->have_grad = false;
@@ -468,6 +475,21 @@ extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
       const int gk = (int)(((long long)nk * (g + 1)) / ng - ((long long)nk * g) / ng);
       c->tcg[g] = tc_plan_create_sharing(c->tc, gk * m, c->status);
     }
+    // the final Rayleigh-Ritz step's products: 6 strain stacks and 3 displacement columns per vector
+    if (c->tc && oz_eligible(N)) {
+      c->oz = oz_plan_create(N, 9 * (int)nvec, c->status, nullptr);
+      for (int g = 1; g < ng && oz_available(c->oz); ++g) {
+        const int gk = (int)(((long long)nk * (g + 1)) / ng - ((long long)nk * g) / ng);
+        c->ozg[g] = oz_plan_create(N, 9 * gk * m, c->status, c->oz);
+      }
+      bool all = oz_available(c->oz);
+      for (int g = 1; g < ng; ++g) all = all && oz_available(c->ozg[g]);
+      if (!all) {  // keep the FP64 GEMM for this k-set
+        for (auto& o : c->ozg)
+          if (o) { oz_plan_destroy(o); o = nullptr; }
+        if (c->oz) { oz_plan_destroy(c->oz); c->oz = nullptr; }
+      }
+    }
   }
   if (rc != PC_OK) { free_kset(c); return PC_ENOMEM; }
   if (cudaMemcpy(c->Q, q, 3 * sizeof(double) * nk, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -507,6 +529,12 @@ extern "C" int pc_set_design(pc_ctx* c, const double* rho, void* stream) {
       rc = tc_prepare_operators(c->tc, c->W, c->T, c->cA, 1.0 / c->sO, s);
       if (rc) return rc;
       c->tc_ready = true;
+    }
+    c->oz_ready = false;
+    if (c->oz) {  // the final step's operators: W in SI (the epilogue scales), T_rho / sO
+      rc = oz_prepare_operators(c->oz, c->W, c->T, 1.0, 1.0 / c->sO, s);
+      if (rc) return rc;
+      c->oz_ready = true;
     }
   }
   PC_CUDA_TRY(cudaEventRecord(c->ev_s1, s));
@@ -556,6 +584,30 @@ static int apply_fp64(pc_ctx* c, const double2* X, double2* AX, double2* OX, int
   return rc;
 }
 
+// The same products as apply_fp64 (operators prepared with Omega scaled by 1/sO) from the
+// operators' exact 6-bit slices on the tensor cores (oz_gemm.cu): FP64-accurate to about 2e-12
+// of the row and column scales.
+static int apply_sliced(pc_ctx* c, OzPlan* oz, const double2* X, double2* AX, double2* OX, int nvec, int m,
+                        const double* Q, double epi, double2* E, double2* S, cudaStream_t s) {
+  const int N = c->N;
+  const double f = 8.0 * (double)N * (double)N;  // algorithmic flops per complex column
+  int rc = launch_strain<double>(X, nvec, m, c->geom, Q, E, s);
+  if (!rc) rc = oz_slice_columns(oz, E, 6 * nvec, 0, s);
+  if (!rc) rc = oz_slice_columns(oz, X, 3 * nvec, 6 * nvec, s);
+  if (rc) return rc;
+  // the three products, one timed launch each: W1 on the dilatation, W2 on the five deviatoric
+  // strain components, T_rho / sO on the displacements
+  const int which[3] = {0, 1, 2}, col0[3] = {0, 1, 6}, cols[3] = {1, 5, 3};
+  double2* out[3] = {S, S + (long long)nvec * N, OX};
+  for (int g = 0; g < 3 && !rc; ++g) {
+    const int slot = ph_begin(c, PH_RR_GEMM, f * cols[g] * nvec, s);
+    rc = oz_gemm(oz, which[g], col0[g] * nvec, cols[g] * nvec, out[g], s);
+    ph_end(c, slot, s);
+  }
+  if (rc) return rc;
+  return launch_epilogue<double>(S, nvec, m, c->geom, Q, epi, epi, AX, s);
+}
+
 // Nondimensional A' X and Omega' X for FP32 vectors (vector v at k = v / m of Q): the split-BF16
 // tensor-core path; the FP32 CUDA-core GEMM only where the tensor-core plan could not be set up.
 static int apply_fp32(pc_ctx* c, const float2* X, float2* AX, float2* OX, int nvec, int m, const double* Q,
@@ -592,6 +644,7 @@ struct KSet {
   int* h_unconv = nullptr;  // pinned host copy
   int unconv = 0, iterations = 0;
   TcPlan* tc = nullptr;     // tensor-core workspaces of this subset
+  OzPlan* oz = nullptr;     // sliced products of this subset's final Rayleigh-Ritz step (or NULL)
 };
 
 template <typename R>
@@ -869,6 +922,7 @@ static int run_split_iteration(pc_ctx* c, cudaStream_t s) {
     ks[g].d_unconv = c->d_unconv + g;
     ks[g].h_unconv = c->h_unconv + g;
     ks[g].tc = g ? c->tcg[g] : c->tc;
+    ks[g].oz = (c->oz_ready && c->oz) ? (g ? c->ozg[g] : c->oz) : nullptr;
     PC_CUDA_TRY(cudaStreamWaitEvent(c->sk[g], c->ev_fork, 0));
   }
   int rcs[kMaxGroups] = {}, dev = 0;
@@ -925,7 +979,10 @@ static int fp64_rayleigh_ritz(pc_ctx* c, const KSet& ks) {
   } else {
     X = (const double2*)c->blk[0] + vo * n3;
   }
-  rc = apply_fp64(c, X, AXd, OXd, (int)nvec, m, c->Q + 3 * k0, c->cA, 1.0 / c->sO, Ed, Sd, s, PH_RR_GEMM);
+  if (ks.oz)
+    rc = apply_sliced(c, ks.oz, X, AXd, OXd, (int)nvec, m, c->Q + 3 * k0, c->cA, Ed, Sd, s);
+  else
+    rc = apply_fp64(c, X, AXd, OXd, (int)nvec, m, c->Q + 3 * k0, c->cA, 1.0 / c->sO, Ed, Sd, s, PH_RR_GEMM);
   if (rc) return rc;
   BlockList<double> A1 = {{X, nullptr, nullptr}}, B1 = {{AXd, nullptr, nullptr}}, B2 = {{OXd, nullptr, nullptr}};
   rc = launch_gram<double>(A1, 1, B1, 1, nk, m, n3, 1.0, gpartd, GAd, s);
@@ -991,6 +1048,7 @@ extern "C" int pc_bands(pc_ctx* c, double* omega, void* stream) {
     ks.d_unconv = c->d_unconv;
     ks.h_unconv = c->h_unconv;
     ks.tc = c->tc;
+    ks.oz = (c->oz_ready && c->oz) ? c->oz : nullptr;
     rc = (c->prm.precision == PC_FP64) ? run_block_iteration<double>(c, ks) : run_block_iteration<float>(c, ks);
     c->iterations = ks.iterations;
     c->unconv = ks.unconv;
@@ -1115,10 +1173,12 @@ extern "C" int pc_get_stats(pc_ctx* c, pc_stats* out) {
   out->ms_rr_gemm = c->ph_ms[PH_RR_GEMM];
   out->rr_gemm_launches = c->ph_count[PH_RR_GEMM];
   out->rr_gemm_flops = c->ph_flops[PH_RR_GEMM];
+  out->rr_sliced = (c->oz_ready && c->oz) ? 1 : 0;
   out->ms_iter_apply = c->ph_ms[PH_ITER_APPLY];
   out->iter_apply_calls = c->ph_count[PH_ITER_APPLY];
   out->iter_apply_flops = c->ph_flops[PH_ITER_APPLY];
   out->ms_small = c->ph_ms[PH_SMALL];
+  out->small_calls = c->ph_count[PH_SMALL];
   out->ms_grad_kernels = c->ph_ms[PH_GRAD];
   out->ms_gram = c->ph_ms[PH_GRAM];
   out->gram_launches = c->ph_count[PH_GRAM];

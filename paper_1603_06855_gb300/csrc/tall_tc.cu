@@ -16,6 +16,7 @@
 #include <math.h>
 #include <string.h>
 #include <vector>
+#include "gemm_tc.h"
 #include "kernels.h"
 #include "tc_ptx.cuh"
 
@@ -648,6 +649,7 @@ extern "C" int pc_check_tensor_kernels(int what, int nk, int m, int nblk, int n3
     *rel_err = (h == PC_ETIMEOUT) ? 0.0 : 1.0;
     return PC_OK;
   }
+  if (what == 3) return oz_self_check(n3, nk * m, rel_err);  // n3: plane waves, nk * m columns
   if (nk < 1 || m < 1 || m > 24 || nblk < 1 || nblk > 3 || n3 < 1 || (what != 0 && what != 1)) return PC_EINVAL;
   *rel_err = -1.0;
   const long long blk = (long long)nk * m * n3;

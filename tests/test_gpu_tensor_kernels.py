@@ -1,4 +1,6 @@
-"""Tensor-core kernels of the FP32 block iteration against the FP32 CUDA-core kernels.
+"""Tensor-core kernels against CUDA-core references: those of the FP32 block iteration against the
+FP32 CUDA-core kernels, and the sliced FP64-accurate products of the final Rayleigh-Ritz step
+against the FP64 GEMM.
 
 The batched Gram product A^H B and the basis update [S] C run on tcgen05 with both operands
 split into three bf16 slices (six slice products, FP32 accumulation in tensor memory).  On
@@ -47,3 +49,14 @@ def test_bounded_wait_expires(B):
     with the CUDA-core ones."""
     assert B.pc_check_tensor_kernels(2, 1, 1, 1, 1) == 0.0
     assert 0 <= B.pc_check_tensor_kernels(0, 2, 8, 1, 64) < TOL
+
+
+@pytest.mark.parametrize("N,ncols", [(729, 300), (343, 70), (125, 33), (27, 5)])
+def test_sliced_fp64_products(B, N, ncols):
+    """The final Rayleigh-Ritz step's FP64-accurate products (exact 6-bit slices of both operands,
+    36 slice products on the tensor cores, FP64 recombination) against the FP64 GEMM on seeded
+    complex data whose operator rows span eight binades: 1e-10 of the largest result entry
+    (measured about 2e-12 of the row and column scales; FP64 itself about 4e-15).  Sizes cover
+    several 128-row and 64-column tiles with ragged tails and fewer rows than one tile."""
+    err = B.pc_check_tensor_kernels(3, 1, ncols, 1, N)
+    assert 0 <= err < 1e-10, err
