@@ -9,7 +9,8 @@
 // centroid from the plane-wave coefficients.  The kernels synthesise the 3 + 6 fields of
 // every weighted (k, band) on the voxel grid by separable sums (axis 2, axis 1 into a
 // scratch array, then axis 0 inside the per-voxel reduction) and reduce the weighted
-// quadratic forms over all (k, band).
+// quadratic forms over all (k, band): per chunk of pairs, then over the chunks in FP64.
+#include <algorithm>
 #include "kernels.h"
 
 // ---------------------------------------------------------------------------
@@ -257,47 +258,98 @@ __global__ void k_adj_synth12(AdjointArgs a) {
   }
 }
 
-// Axis-0 synthesis fused with the weighted reduction over (k, band); the sum over pairs is
-// accumulated in FP64.
-template <typename R, int M2>
-__global__ void k_adj_reduce(AdjointArgs a) {
+// Axis-0 synthesis fused with the weighted reduction over (k, band).  The pairs are cut into
+// chunks along the grid's z; each thread synthesises VPT voxels along axis 0 at one (j, l), so
+// that every loaded axis-1/2 coefficient feeds VPT complex FMAs, and sums its chunk's three
+// weighted quadratic forms in R (FP32 in the mixed form: about a hundred pairs per chunk).  The
+// chunk sums go to part[chunk][3][ne]; k_adj_finish adds them in FP64 in chunk order.
+constexpr int kAdjReduceThreads = 128;  // at 166 registers (M2 = 9, 4 voxels) three blocks per SM
+
+template <typename R, int M2, int VPT>
+__global__ __launch_bounds__(kAdjReduceThreads) void k_adj_reduce(AdjointArgs a, int chunk) {
   typedef typename cplx_t<R>::type C2;
   const int n0 = a.n0, n1 = a.n1, n2 = a.n2;
+  const int nig = (n0 + VPT - 1) / VPT;
   const int j = blockIdx.y;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= n0 * n2) return;
-  const int i = v / n2, l = v % n2;
-  C2 ph[M2];  // compile-time size and fully unrolled loops keep these in registers
+  if (v >= nig * n2) return;
+  const int ig = v / n2, l = v % n2;
+  C2 ph[VPT][M2];  // compile-time sizes and fully unrolled loops keep these in registers
 #pragma unroll
-  for (int g = 0; g < M2; ++g) ph[g] = from_d2<R>(phase_pi_over((long long)(g - a.M) * (2 * i + 1), n0));
+  for (int s = 0; s < VPT; ++s) {
+    const int i = min(ig * VPT + s, n0 - 1);
+#pragma unroll
+    for (int g = 0; g < M2; ++g) ph[s][g] = from_d2<R>(phase_pi_over((long long)(g - a.M) * (2 * i + 1), n0));
+  }
   const int np = *a.npairs;
+  const int p0 = blockIdx.z * chunk, p1 = min(np, p0 + chunk);
   const long long fstride = (long long)M2 * n1 * n2;
   const long long gstride = (long long)n1 * n2;
   const C2* t2 = (const C2*)a.t2;
   // the compliance part's factors d f1/d chi, d f2/d chi belong to the element: three weighted sums
-  double acc_m = 0.0, acc_1 = 0.0, acc_2 = 0.0;
-  for (int p = 0; p < np; ++p) {
+  R acc_m[VPT], acc_1[VPT], acc_2[VPT];
+#pragma unroll
+  for (int s = 0; s < VPT; ++s) acc_m[s] = acc_1[s] = acc_2[s] = (R)0;
+  for (int p = p0; p < p1; ++p) {
     const int pr = a.pairs[p];
-    const double w = a.weights[pr];
-    const double lam = a.lam[pr] * a.lref;
+    const double wd = a.weights[pr];
+    const R w = (R)wd, wl = (R)(wd * a.lam[pr] * a.lref);
     const C2* base = t2 + (long long)p * 9 * fstride + (long long)j * n2 + l;
-    R q[9];
+    R u2[VPT], sd[VPT], q3[VPT];
+#pragma unroll
+    for (int s = 0; s < VPT; ++s) u2[s] = sd[s] = q3[s] = (R)0;
 #pragma unroll
     for (int f = 0; f < 9; ++f) {
-      C2 s = mk<R>(0, 0);
       const C2* srcf = base + f * fstride;
+      C2 x[M2];
 #pragma unroll
-      for (int g = 0; g < M2; ++g) cfma(s, srcf[g * gstride], ph[g]);
-      q[f] = s.x * s.x + s.y * s.y;
+      for (int g = 0; g < M2; ++g) x[g] = srcf[g * gstride];
+#pragma unroll
+      for (int s = 0; s < VPT; ++s) {
+        C2 z = mk<R>(0, 0);
+#pragma unroll
+        for (int g = 0; g < M2; ++g) cfma(z, x[g], ph[s][g]);
+        const R q = z.x * z.x + z.y * z.y;
+        if (f < 3) u2[s] += q;
+        else if (f == 3) q3[s] = q;
+        else sd[s] += q;
+      }
     }
-    double u2 = (double)q[0] + q[1] + q[2];
-    double sd = (double)q[4] + q[5] + q[6] + q[7] + q[8];
-    acc_m += w * lam * u2;
-    acc_1 += w * (double)q[3];
-    acc_2 += w * sd;
+#pragma unroll
+    for (int s = 0; s < VPT; ++s) {
+      acc_m[s] += wl * u2[s];
+      acc_1[s] += w * q3[s];
+      acc_2[s] += w * sd[s];
+    }
   }
-  const long long e = ((long long)i * n1 + j) * n2 + l;
   const long long ne = (long long)n0 * n1 * n2;
+  R* part = (R*)a.part + (long long)blockIdx.z * 3 * ne;
+#pragma unroll
+  for (int s = 0; s < VPT; ++s) {
+    const int i = ig * VPT + s;
+    if (i < n0) {
+      const long long e = ((long long)i * n1 + j) * n2 + l;
+      part[e] = acc_m[s];
+      part[ne + e] = acc_1[s];
+      part[2 * ne + e] = acc_2[s];
+    }
+  }
+}
+
+// The chunk sums added in FP64 and combined with the per-element factors.
+template <typename R>
+__global__ void k_adj_finish(AdjointArgs a, int nchunks) {
+  const long long ne = (long long)a.n0 * a.n1 * a.n2;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const R* part = (const R*)a.part;
+  double acc_m = 0.0, acc_1 = 0.0, acc_2 = 0.0;
+  for (int c = 0; c < nchunks; ++c) {
+    const R* pc = part + (long long)c * 3 * ne;
+    acc_m += (double)pc[e];
+    acc_1 += (double)pc[ne + e];
+    acc_2 += (double)pc[2 * ne + e];
+  }
   const double acc = -a.d_rho * acc_m - a.two_pi_V_sq * (a.dfc[e] * acc_1 + a.dfc[ne + e] * acc_2);
   a.grad[e] = acc * a.inv_sO * a.ve * a.dchi[e];
 }
@@ -307,6 +359,11 @@ size_t adjoint_staging_bytes(int M, int n1, int n2, bool fp32) {
   const size_t elems = M2 * M2 * M2 + M2 * M2 * (size_t)n2 + M2 * (size_t)n2 + M2 * (size_t)n1;
   return elems * (fp32 ? sizeof(float2) : sizeof(double2));
 }
+
+// Voxels per thread of the reduction: 4 in FP32 (2 at M2 = 11), 1 in FP64 (register budget of
+// the phase tables).
+template <typename R>
+constexpr int adj_vpt(int M2) { return sizeof(R) == sizeof(float) ? (M2 <= 9 ? 4 : 2) : 1; }
 
 template <typename R>
 static int launch_adjoint_t(const AdjointArgs& a, cudaStream_t s) {
@@ -322,14 +379,32 @@ static int launch_adjoint_t(const AdjointArgs& a, cudaStream_t s) {
   dim3 g1(a.max_pairs, 9);
   k_adj_synth12<R><<<g1, 256, sm, s>>>(a);
   PC_LAUNCH_CHECK();
-  dim3 g2(cdiv((long long)a.n0 * a.n2, 256), a.n1);
+  const int vpt = M2 <= 9 ? adj_vpt<R>(9) : adj_vpt<R>(11);
+  const long long gx = cdiv((long long)cdiv(a.n0, vpt) * a.n2, kAdjReduceThreads);
+  // enough pair chunks for about six blocks per SM; the chunks cover max_pairs, and the ones
+  // past the device's pair count write zeros
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cudaGetLastError();
+    return n;
+  }();
+  int nchunks = (int)std::min<long long>(kAdjChunksMax, std::max<long long>(1, cdiv(6LL * sms, gx * a.n1)));
+  nchunks = std::max(1, std::min(nchunks, a.max_pairs));
+  const int chunk = (int)cdiv(a.max_pairs, nchunks);
+  nchunks = (int)cdiv(a.max_pairs, chunk);
+  dim3 g2((unsigned)gx, a.n1, nchunks);
   switch (M2) {
-    case 3: k_adj_reduce<R, 3><<<g2, 256, 0, s>>>(a); break;
-    case 5: k_adj_reduce<R, 5><<<g2, 256, 0, s>>>(a); break;
-    case 7: k_adj_reduce<R, 7><<<g2, 256, 0, s>>>(a); break;
-    case 9: k_adj_reduce<R, 9><<<g2, 256, 0, s>>>(a); break;
-    default: k_adj_reduce<R, 11><<<g2, 256, 0, s>>>(a); break;
+    case 3: k_adj_reduce<R, 3, adj_vpt<R>(3)><<<g2, kAdjReduceThreads, 0, s>>>(a, chunk); break;
+    case 5: k_adj_reduce<R, 5, adj_vpt<R>(5)><<<g2, kAdjReduceThreads, 0, s>>>(a, chunk); break;
+    case 7: k_adj_reduce<R, 7, adj_vpt<R>(7)><<<g2, kAdjReduceThreads, 0, s>>>(a, chunk); break;
+    case 9: k_adj_reduce<R, 9, adj_vpt<R>(9)><<<g2, kAdjReduceThreads, 0, s>>>(a, chunk); break;
+    default: k_adj_reduce<R, 11, adj_vpt<R>(11)><<<g2, kAdjReduceThreads, 0, s>>>(a, chunk); break;
   }
+  PC_LAUNCH_CHECK();
+  const long long ne = (long long)a.n0 * a.n1 * a.n2;
+  k_adj_finish<R><<<(unsigned)cdiv(ne, 256), 256, 0, s>>>(a, nchunks);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }

@@ -172,8 +172,10 @@ struct AdjointArgs {
   double ve;             // element volume
   const double* dchi;
   void* t2;              // scratch: max_pairs x 9 x M2 x n1 x n2 complex (FP64 or FP32)
+  void* part;            // scratch: kAdjChunksMax x 3 x ne chunk sums (FP64 or FP32)
   double* grad;
 };
+constexpr int kAdjChunksMax = 32;  // pair chunks of the adjoint's reduction
 // fp32: synthesis in FP32 (mixed form); the weighted sum is accumulated in FP64 either way.
 int launch_adjoint(const AdjointArgs& a, bool fp32, cudaStream_t s);
 // Dynamic shared memory of the adjoint's field-synthesis kernel: the N coefficients of one

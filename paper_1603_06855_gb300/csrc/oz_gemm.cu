@@ -200,14 +200,22 @@ __global__ __launch_bounds__(192, 1) void k_oz_gemm(const __grid_constant__ CUte
 // share the magnitudes of complex row p) or per column (a complex vector of length N, real K
 // index 2q + {re, im}).  Slice i of row/column x is written at out + i * slice_stride + x * Kp;
 // K positions past 2N are zero.
-__device__ __forceinline__ void slice8(double v, double inv_scale, __nv_bfloat16 q[OZ_S]) {
-  double r = v * inv_scale;  // |r| <= 1/2
+// The eight 6-bit slices of v / 2^e (|v| 2^-e <= 1/2): I = rint(v 2^-e 2^48) as a 64-bit integer,
+// then balanced base-64 digits from the least significant up (each in [-32, 31], the leading one
+// in [-32, 32]), so that sum_i q_i 2^-6i = I 2^-48.  This is the value the successive cuts
+// q_i = rint((r - sum_{l<i} q_l 2^-6l) 2^6i) represent: the parts already cut are multiples of
+// 2^-42, so the last cut rounds r 2^48 shifted by a multiple of 64, which changes neither the
+// rounding nor a tie's parity.  Integer work only after one multiply and one conversion.
+__device__ __forceinline__ void slice8(double v, double inv_scale48, int q[OZ_S]) {
+  long long I = __double2ll_rn(v * inv_scale48);  // the multiply is by a power of two: exact
 #pragma unroll
-  for (int i = 1; i <= OZ_S; ++i) {
-    const double qi = rint(ldexp(r, 6 * i));
-    r -= ldexp(qi, -6 * i);  // exact: qi 2^-6i shares the binade of r's leading bits
-    q[i - 1] = __float2bfloat16_rn((float)qi);
+  for (int i = OZ_S - 1; i > 0; --i) {
+    int d = (int)(I & 63);
+    d -= (d >= 32) ? 64 : 0;
+    q[i] = d;
+    I = (I - d) >> 6;
   }
+  q[0] = (int)I;
 }
 
 // Power of two 2^e with max |x| 2^-e in (1/4, 1/2] (1 for an all-zero row).
@@ -218,14 +226,36 @@ __device__ __forceinline__ double pow2_scale(double mx) {
   return ldexp(1.0, e + 1);
 }
 
+// Four consecutive K entries (two complex values) of one row or column, sliced and stored as
+// 8 bytes per slice.
+__device__ __forceinline__ void store_slices4(const double v[4], double inv48, __nv_bfloat16* dst,
+                                              long long sstride) {
+  int q[4][OZ_S];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) slice8(v[e], inv48, q[e]);
+#pragma unroll
+  for (int i = 0; i < OZ_S; ++i) {
+    __nv_bfloat162 lo = __floats2bfloat162_rn((float)q[0][i], (float)q[1][i]);
+    __nv_bfloat162 hi = __floats2bfloat162_rn((float)q[2][i], (float)q[3][i]);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t*>(&lo);
+    u.y = *reinterpret_cast<uint32_t*>(&hi);
+    *reinterpret_cast<uint2*>(dst + i * sstride) = u;
+  }
+}
+
+// One warp per real row of alpha W (rows 2p, 2p + 1 of [[Re, -Im], [Im, Re]]); rows beyond 2N and
+// columns beyond 2N are zero.  Kp is a multiple of 32, so every 4-entry group is 8-byte aligned.
 __global__ void k_oz_slice_rows(const double2* __restrict__ W, int N, double alpha, int Mp, int Kp,
                                 __nv_bfloat16* __restrict__ out, double* __restrict__ row_scale) {
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (row >= Mp) return;
   const long long sstride = (long long)Mp * Kp;
+  __nv_bfloat16* o = out + (long long)row * Kp;
   if (row >= 2 * N) {
-    for (int k = lane; k < Kp; k += 32)
-      for (int i = 0; i < OZ_S; ++i) out[i * sstride + (long long)row * Kp + k] = __float2bfloat16_rn(0.f);
+    const uint2 z = make_uint2(0u, 0u);
+    for (int k = 4 * lane; k < Kp; k += 128)
+      for (int i = 0; i < OZ_S; ++i) *reinterpret_cast<uint2*>(o + i * sstride + k) = z;
     if (lane == 0) row_scale[row] = 0.0;
     return;
   }
@@ -233,22 +263,23 @@ __global__ void k_oz_slice_rows(const double2* __restrict__ W, int N, double alp
   const double2* w = W + (long long)p * N;
   double mx = 0.0;
   for (int q = lane; q < N; q += 32) mx = fmax(mx, fmax(fabs(w[q].x), fabs(w[q].y)) * fabs(alpha));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  const double sc = pow2_scale(mx), inv = 1.0 / sc;
-  for (int k = lane; k < Kp; k += 32) {
-    double v = 0.0;
-    if (k < 2 * N) {
-      const double2 z = w[k >> 1];
-      const int rp = k & 1;  // [[Re, -Im], [Im, Re]]
-      v = alpha * ((r == rp) ? z.x : (r == 0 ? -z.y : z.y));
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  const double sc = pow2_scale(mx), inv48 = ldexp(1.0 / sc, 48);
+  for (int k = 4 * lane; k < Kp; k += 128) {
+    double v[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = (k >> 1) + h;
+      const double2 z = q < N ? w[q] : make_double2(0.0, 0.0);
+      v[2 * h] = alpha * (r == 0 ? z.x : z.y);       // column 2q: Re z (row 2p), Im z (row 2p + 1)
+      v[2 * h + 1] = alpha * (r == 0 ? -z.y : z.x);  // column 2q + 1: -Im z, Re z
     }
-    __nv_bfloat16 q[OZ_S];
-    slice8(v, inv, q);
-    for (int i = 0; i < OZ_S; ++i) out[i * sstride + (long long)row * Kp + k] = q[i];
+    store_slices4(v, inv48, o + k, sstride);
   }
   if (lane == 0) row_scale[row] = sc;
 }
 
+// One warp per complex column of X (real entries Re, Im interleaved along K); entries beyond 2N are zero.
 __global__ void k_oz_slice_cols(const double2* __restrict__ X, int ncols, int N, int Kp, long long sstride,
                                 int col_off, __nv_bfloat16* __restrict__ out, double* __restrict__ col_scale) {
   const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
@@ -256,14 +287,16 @@ __global__ void k_oz_slice_cols(const double2* __restrict__ X, int ncols, int N,
   const double2* x = X + (long long)c * N;
   double mx = 0.0;
   for (int q = lane; q < N; q += 32) mx = fmax(mx, fmax(fabs(x[q].x), fabs(x[q].y)));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  const double sc = pow2_scale(mx), inv = 1.0 / sc;
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  const double sc = pow2_scale(mx), inv48 = ldexp(1.0 / sc, 48);
   const long long cc = (long long)col_off + c;
-  for (int k = lane; k < Kp; k += 32) {
-    const double v = (k < 2 * N) ? ((k & 1) ? x[k >> 1].y : x[k >> 1].x) : 0.0;
-    __nv_bfloat16 q[OZ_S];
-    slice8(v, inv, q);
-    for (int i = 0; i < OZ_S; ++i) out[i * sstride + cc * Kp + k] = q[i];
+  __nv_bfloat16* o = out + cc * Kp;
+  for (int k = 4 * lane; k < Kp; k += 128) {
+    const int q = k >> 1;
+    const double2 z0 = q < N ? x[q] : make_double2(0.0, 0.0);
+    const double2 z1 = q + 1 < N ? x[q + 1] : make_double2(0.0, 0.0);
+    const double v[4] = {z0.x, z0.y, z1.x, z1.y};
+    store_slices4(v, inv48, o + k, sstride);
   }
   if (lane == 0) col_scale[cc] = sc;
 }

@@ -86,6 +86,7 @@ struct pc_ctx {
   double *weights = nullptr;
   int *pairs = nullptr, *npairs = nullptr;
   double2* adj_t2 = nullptr;
+  double* adj_part = nullptr;  // chunk sums of the adjoint's reduction
   TcPlan* tc = nullptr;
   TcPlan* tcg[kMaxGroups] = {};  // workspaces of k groups 1.. (operators shared with tc)
   OzPlan* oz = nullptr;          // sliced FP64-accurate operators of the final Rayleigh-Ritz step (mixed form)
@@ -236,7 +237,7 @@ static void free_kset(pc_ctx* c) {
   dfree(c->Xd); dfree(c->AXd); dfree(c->OXd); dfree(c->Ed); dfree(c->Sd); dfree(c->Th); dfree(c->St);
   dfree(c->gpartd); dfree(c->GAd); dfree(c->GOd); dfree(c->Cd);
   dfree(c->lamd); dfree(c->lam_nd); dfree(c->rnormd); dfree(c->actived);
-  dfree(c->weights); dfree(c->pairs); dfree(c->npairs); dfree(c->adj_t2);
+  dfree(c->weights); dfree(c->pairs); dfree(c->npairs); dfree(c->adj_t2); dfree(c->adj_part);
   for (auto& t : c->tcg)
     if (t) { tc_plan_destroy(t); t = nullptr; }
   if (c->tc) { tc_plan_destroy(c->tc); c->tc = nullptr; }
@@ -465,6 +466,7 @@ extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
   rc |= dalloc(&c->pairs, (size_t)nk * c->nb);
   rc |= dalloc(&c->npairs, 1);
   rc |= dalloc(&c->adj_t2, (size_t)nk * c->nb * 9 * c->M2 * c->prm.n[1] * c->prm.n[2]);
+  rc |= dalloc(&c->adj_part, (size_t)kAdjChunksMax * 3 * c->prm.n[0] * c->prm.n[1] * c->prm.n[2]);
   if (rc == PC_OK && c->prm.precision == PC_MIXED) {
     c->tc = tc_plan_create(N, (int)nvec, c->status);
     c->tc_ready = false;
@@ -1112,6 +1114,7 @@ static int gap_and_grad_impl(pc_ctx* c, int n_lower, int mode, double beta, cons
     a.ve = c->ve;
     a.dchi = c->dchi;
     a.t2 = c->adj_t2;
+    a.part = c->adj_part;
     a.grad = grad;
     int sl = ph_begin(c, PH_GRAD, 0.0, s);
     rc = launch_adjoint(a, c->prm.precision == PC_MIXED, s);
