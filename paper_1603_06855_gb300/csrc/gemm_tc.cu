@@ -39,10 +39,14 @@ constexpr int SMEM_BYTES = TC_STAGES * STAGE_BYTES + 1024 /* barriers */ + 1024 
 // Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N = TC_BN.
 __host__ __device__ constexpr uint32_t idesc_bf16() { return idesc_bf16_n(TC_BN); }
 
-// Persistent: each CTA walks the output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
-// (M-fastest, so CTAs working at the same time share the B column tile in L2).  The stage
-// ring runs on across tiles, and the accumulator alternates between two 128-column halves of
-// tensor memory, so the epilogue warps drain tile i while the MMAs of tile i + 1 run.
+// Persistent: the producer lane claims output tiles from a counter in global memory (M-fastest,
+// so CTAs working at the same time share the B column tile in L2) and hands each tile index to
+// the MMA lane and the epilogue warps through a 4-deep ring in shared memory; an index >= tiles
+// ends all three.  CTAs that start late, behind another stream's kernel on their SM, claim fewer
+// tiles instead of holding the launch up.  The last CTA to finish resets the counter for the
+// next launch on the same stream.  The stage ring runs on across tiles, and the accumulator
+// alternates between two 128-column halves of tensor memory, so the epilogue warps drain tile i
+// while the MMAs of tile i + 1 run.
 __global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUtensorMap tA_hi,
                                                     const __grid_constant__ CUtensorMap tA_mid,
                                                     const __grid_constant__ CUtensorMap tA_lo,
@@ -50,14 +54,17 @@ __global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUte
                                                     const __grid_constant__ CUtensorMap tB_mid,
                                                     const __grid_constant__ CUtensorMap tB_lo, int num_kb, int col_base,
                                                     int ncols, int m_valid, int mtiles, int ntiles,
-                                                    float* __restrict__ C, long long ldc, int* status) {
+                                                    float* __restrict__ C, long long ldc, int* tile_ctr,
+                                                    int* status) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* gbase = smem_raw + (base - raw);
   const uint32_t bars = base + TC_STAGES * STAGE_BYTES;
-  // barriers: full[s] +8s, empty[s] +64+8s, tfull[b] +128+8b, tempty[b] +160+8b, done +192; tmem slot +256
+  // barriers: full[s] +8s, empty[s] +64+8s, tfull[b] +128+8b, tempty[b] +160+8b, done +192; tmem slot +256;
+  // tile ring: idfull[j] +320+8j, idempty[j] +352+8j, tile index j at +384+4j
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + TC_STAGES * STAGE_BYTES + 256);
+  volatile int* tile_id = reinterpret_cast<volatile int*>(gbase + TC_STAGES * STAGE_BYTES + 384);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles = mtiles * ntiles;
 
@@ -71,6 +78,10 @@ __global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUte
       mbar_init(bars + 160 + 8 * b, 128);
     }
     mbar_init(bars + 192, 1);
+    for (int j = 0; j < 4; ++j) {
+      mbar_init(bars + 320 + 8 * j, 1);
+      mbar_init(bars + 352 + 8 * j, 5);  // the MMA lane and the four epilogue warps
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -88,7 +99,13 @@ __global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUte
     if (lane == 0) {
       long long it = 0;  // stage counter across tiles
       bool ok = true;
-      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      for (int tl = 0; ok; ++tl) {
+        const int slot = tl & 3;
+        if (!(ok = mbar_wait(bars + 352 + 8 * slot, ((uint32_t)(tl >> 2) & 1u) ^ 1u, status))) break;
+        const int t = atomicAdd(tile_ctr, 1);
+        tile_id[slot] = t;
+        mbar_arrive(bars + 320 + 8 * slot);
+        if (t >= tiles) break;
         const int m0 = (t % mtiles) * TC_BM, n0 = (t / mtiles) * TC_BN;
         for (int kb = 0; kb < num_kb; ++kb, ++it) {
           const int s = (int)(it % TC_STAGES);
@@ -110,8 +127,12 @@ __global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUte
       const uint32_t idesc = idesc_bf16();
       long long it = 0;
       bool ok = true;
-      int tl = 0;  // local tile index
-      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
+      for (int tl = 0; ok; ++tl) {  // tl: local tile index
+        const int slot = tl & 3;
+        if (!(ok = mbar_wait(bars + 320 + 8 * slot, (uint32_t)(tl >> 2) & 1u, status))) break;
+        const int t = tile_id[slot];
+        mbar_arrive(bars + 352 + 8 * slot);
+        if (t >= tiles) break;
         const int b = tl & 1;
         // accumulator half b must have been drained (its use tl / 2 - 1)
         if (!(ok = mbar_wait(bars + 160 + 8 * b, ((uint32_t)(tl >> 1) & 1u) ^ 1u, status))) break;
@@ -146,8 +167,13 @@ __global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUte
   } else {
     // epilogue warps 2..5: lane quadrant (warp % 4) of the accumulator
     const int quad = warp & 3;
-    int tl = 0;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
+    for (int tl = 0;; ++tl) {
+      const int slot = tl & 3;
+      if (!__all_sync(0xffffffffu, mbar_wait(bars + 320 + 8 * slot, (uint32_t)(tl >> 2) & 1u, status))) break;
+      const int t = tile_id[slot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bars + 352 + 8 * slot);
+      if (t >= tiles) break;
       const int b = tl & 1;
       const bool ok = __all_sync(0xffffffffu, mbar_wait(bars + 128 + 8 * b, (uint32_t)(tl >> 1) & 1u, status));
       tc_fence_after();
@@ -175,6 +201,13 @@ __global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUte
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * TC_BN))
                  : "memory");
+  }
+  if (threadIdx.x == 0) {  // every claim of this CTA is done; the last CTA resets the counter
+    __threadfence();
+    if (atomicAdd(tile_ctr + 1, 1) == (int)gridDim.x - 1) {
+      atomicExch(tile_ctr, 0);
+      atomicExch(tile_ctr + 1, 0);
+    }
   }
 }
 
@@ -293,6 +326,7 @@ struct TcPlan {
   float2* S;              // FP32 stress stacks [6][nvec][N]
   CUtensorMap mA_hi[3], mA_mid[3], mA_lo[3], mE[3], mX[3];
   int* status;
+  int* tile_ctr;          // tile counter of k_tc_gemm and its finished-CTA count (zero between launches)
   bool ok;
   bool owns_ops;          // false: the operator slices belong to another plan
 };
@@ -317,6 +351,7 @@ TcPlan* tc_plan_create(int N, int nvec, int* status) {
   good &= cudaMalloc(&p->E, 3 * esz * 2) == cudaSuccess;
   good &= cudaMalloc(&p->X, 3 * xsz * 2) == cudaSuccess;
   good &= cudaMalloc(&p->S, (size_t)6 * nvec * N * sizeof(float2)) == cudaSuccess;
+  good &= cudaMalloc(&p->tile_ctr, 2 * sizeof(int)) == cudaSuccess && cudaMemset(p->tile_ctr, 0, 2 * sizeof(int)) == cudaSuccess;
   if (!good) {
     cudaGetLastError();
     tc_plan_destroy(p);
@@ -350,6 +385,7 @@ void tc_plan_destroy(TcPlan* p) {
   if (p->E) cudaFree(p->E);
   if (p->X) cudaFree(p->X);
   if (p->S) cudaFree(p->S);
+  if (p->tile_ctr) cudaFree(p->tile_ctr);
   delete p;
 }
 
@@ -377,6 +413,7 @@ TcPlan* tc_plan_create_sharing(const TcPlan* ops, int nvec, int* status) {
   bool good = cudaMalloc(&p->E, 3 * esz * 2) == cudaSuccess;
   good &= cudaMalloc(&p->X, 3 * xsz * 2) == cudaSuccess;
   good &= cudaMalloc(&p->S, (size_t)6 * nvec * p->N * sizeof(float2)) == cudaSuccess;
+  good &= cudaMalloc(&p->tile_ctr, 2 * sizeof(int)) == cudaSuccess && cudaMemset(p->tile_ctr, 0, 2 * sizeof(int)) == cudaSuccess;
   if (!good) {
     cudaGetLastError();
     tc_plan_destroy(p);
@@ -416,7 +453,7 @@ static int launch_tc_gemm(TcPlan* p, int which_A, const CUtensorMap* b, int col_
   const int grid = std::min(mtiles * ntiles, sms);
   k_tc_gemm<<<grid, 192, SMEM_BYTES, s>>>(p->mA_hi[which_A], p->mA_mid[which_A], p->mA_lo[which_A], b[0], b[1], b[2],
                                           p->Kp / TC_BK, col_base, ncols, 2 * p->N, mtiles, ntiles, C, 2LL * p->N,
-                                          p->status);
+                                          p->tile_ctr, p->status);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }

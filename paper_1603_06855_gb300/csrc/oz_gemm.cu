@@ -19,7 +19,8 @@
 // at rows i * Mp.., of B at rows i * ncap..), TMA loads with the 64-byte swizzle (32 bf16 per
 // row), a 2-stage ring of 8 + 8 slice tiles; warp 0 loads, warp 1 issues the 36 x 2 MMAs
 // (kind::f16, M = 128, N = 64, K = 16) per stage, warps 2-5 drain and combine.  Persistent: one CTA
-// per SM walks the output tiles.  Every mbarrier wait is bounded (PC_ETIMEOUT on expiry).
+// per SM; the load lane claims tiles from a counter and hands them on through a ring in shared
+// memory, as in gemm_tc.cu.  Every mbarrier wait is bounded (PC_ETIMEOUT on expiry).
 #include <algorithm>
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -58,14 +59,16 @@ __global__ __launch_bounds__(192, 1) void k_oz_gemm(const __grid_constant__ CUte
                                                     int num_kb, int col_base, int ncols, int m_valid, int mtiles,
                                                     int ntiles, const double* __restrict__ row_scale,
                                                     const double* __restrict__ col_scale, double* __restrict__ C,
-                                                    long long ldc, int* status) {
+                                                    long long ldc, int* tile_ctr, int* status) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* gbase = smem_raw + (base - raw);
   const uint32_t bars = base + OZ_STAGES * OZ_STAGE;
-  // barriers: full[s] +8s, empty[s] +64+8s, tfull +128, tempty +160, done +192; tmem slot +256
+  // barriers: full[s] +8s, empty[s] +64+8s, tfull +128, tempty +160, done +192; tmem slot +256;
+  // tile ring: idfull[j] +320+8j, idempty[j] +352+8j, tile index j at +384+4j
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + OZ_STAGES * OZ_STAGE + 256);
+  volatile int* tile_id = reinterpret_cast<volatile int*>(gbase + OZ_STAGES * OZ_STAGE + 384);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles = mtiles * ntiles;
 
@@ -77,6 +80,10 @@ __global__ __launch_bounds__(192, 1) void k_oz_gemm(const __grid_constant__ CUte
     mbar_init(bars + 128, 1);
     mbar_init(bars + 160, 128);
     mbar_init(bars + 192, 1);
+    for (int j = 0; j < 4; ++j) {
+      mbar_init(bars + 320 + 8 * j, 1);
+      mbar_init(bars + 352 + 8 * j, 5);  // the MMA lane and the four epilogue warps
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -94,7 +101,13 @@ __global__ __launch_bounds__(192, 1) void k_oz_gemm(const __grid_constant__ CUte
     if (lane == 0) {
       long long it = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      for (int tl = 0; ok; ++tl) {
+        const int slot = tl & 3;
+        if (!(ok = mbar_wait(bars + 352 + 8 * slot, ((uint32_t)(tl >> 2) & 1u) ^ 1u, status))) break;
+        const int t = atomicAdd(tile_ctr, 1);
+        tile_id[slot] = t;
+        mbar_arrive(bars + 320 + 8 * slot);
+        if (t >= tiles) break;
         const int m0 = (t % mtiles) * OZ_BM, n0 = (t / mtiles) * OZ_BN;
         for (int kb = 0; kb < num_kb; ++kb, ++it) {
           const int s = (int)(it % OZ_STAGES);
@@ -116,8 +129,12 @@ __global__ __launch_bounds__(192, 1) void k_oz_gemm(const __grid_constant__ CUte
       const uint32_t idesc = idesc_bf16_n(OZ_BN);
       long long it = 0;
       bool ok = true;
-      int tl = 0;
-      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
+      for (int tl = 0; ok; ++tl) {  // tl: local tile index
+        const int slot = tl & 3;
+        if (!(ok = mbar_wait(bars + 320 + 8 * slot, (uint32_t)(tl >> 2) & 1u, status))) break;
+        const int t = tile_id[slot];
+        mbar_arrive(bars + 352 + 8 * slot);
+        if (t >= tiles) break;
         // the accumulators must have been drained (use tl - 1)
         if (!(ok = mbar_wait(bars + 160, ((uint32_t)tl & 1u) ^ 1u, status))) break;
         tc_fence_after();
@@ -153,8 +170,13 @@ __global__ __launch_bounds__(192, 1) void k_oz_gemm(const __grid_constant__ CUte
   } else {
     // epilogue warps 2..5: lane quadrant (warp % 4) of the accumulators
     const int quad = warp & 3;
-    int tl = 0;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
+    for (int tl = 0;; ++tl) {
+      const int slot = tl & 3;
+      if (!__all_sync(0xffffffffu, mbar_wait(bars + 320 + 8 * slot, (uint32_t)(tl >> 2) & 1u, status))) break;
+      const int t = tile_id[slot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bars + 352 + 8 * slot);
+      if (t >= tiles) break;
       const bool ok = __all_sync(0xffffffffu, mbar_wait(bars + 128, (uint32_t)tl & 1u, status));
       tc_fence_after();
       const int row = (t % mtiles) * OZ_BM + quad * 32 + lane;
@@ -192,6 +214,13 @@ __global__ __launch_bounds__(192, 1) void k_oz_gemm(const __grid_constant__ CUte
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(OZ_NACC * OZ_BN))
                  : "memory");
+  }
+  if (threadIdx.x == 0) {  // every claim of this CTA is done; the last CTA resets the counter
+    __threadfence();
+    if (atomicAdd(tile_ctr + 1, 1) == (int)gridDim.x - 1) {
+      atomicExch(tile_ctr, 0);
+      atomicExch(tile_ctr + 1, 0);
+    }
   }
 }
 
@@ -353,6 +382,7 @@ struct OzPlan {
   double* cs = nullptr;                               // column scales (ncap)
   CUtensorMap mA[3], mB;
   int* status = nullptr;
+  int* tile_ctr = nullptr;                            // tile counter and finished-CTA count of k_oz_gemm
   bool ok = false, owns_ops = true;
 };
 
@@ -383,6 +413,7 @@ OzPlan* oz_plan_create(int N, int ncap, int* status, const OzPlan* share) {
   }
   good &= cudaMalloc(&p->Bs, (size_t)OZ_S * p->ncap * p->Kp * 2) == cudaSuccess;
   good &= cudaMalloc(&p->cs, sizeof(double) * p->ncap) == cudaSuccess;
+  good &= cudaMalloc(&p->tile_ctr, 2 * sizeof(int)) == cudaSuccess && cudaMemset(p->tile_ctr, 0, 2 * sizeof(int)) == cudaSuccess;
   if (!good) {
     cudaGetLastError();
     oz_plan_destroy(p);
@@ -407,6 +438,7 @@ void oz_plan_destroy(OzPlan* p) {
   }
   if (p->Bs) cudaFree(p->Bs);
   if (p->cs) cudaFree(p->cs);
+  if (p->tile_ctr) cudaFree(p->tile_ctr);
   delete p;
 }
 
@@ -439,7 +471,7 @@ int oz_gemm(OzPlan* p, int which_A, int col_base, int ncols, double2* C, cudaStr
   // output column c (right-hand side column col_base + c) at C + c N
   k_oz_gemm<<<grid, 192, OZ_SMEM, s>>>(p->mA[which_A], p->mB, p->Mp, p->ncap, p->Kp / OZ_BK, col_base, ncols,
                                        2 * p->N, mtiles, ntiles, p->rs[which_A], p->cs, reinterpret_cast<double*>(C),
-                                       2LL * p->N, p->status);
+                                       2LL * p->N, p->tile_ctr, p->status);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }

@@ -226,7 +226,8 @@ __global__ __launch_bounds__(SR_THREADS) void k_small_rr32(const float2* __restr
     B0[i * SR_LD + c] = make_float2((b1.x + b2.x) * s, (b1.y - b2.y) * s);
     Vt[i * SR_LD + c] = make_float2(i == c ? 1.f : 0.f, 0.f);
   }
-  for (int i = tid; i < n; i += blockDim.x) Vt[i * SR_LD + n] = make_float2(0.f, 0.f);  // padding column
+  for (int t = tid; t < n * (SR_NMAX - n); t += blockDim.x)  // padding columns n .. 71
+    Vt[(t / (SR_NMAX - n)) * SR_LD + n + t % (SR_NMAX - n)] = make_float2(0.f, 0.f);
   __syncthreads();
   // 2. blocked Cholesky of B0 (lower)
   for (int j0 = 0; j0 < n; j0 += SR_PB) {
@@ -355,13 +356,21 @@ __global__ __launch_bounds__(SR_THREADS) void k_small_rr32(const float2* __restr
     pl[tid] = make_plane(B1[u * SR_LD + u].x, B1[v * SR_LD + v].x, B1[u * SR_LD + v], floor_abs, valid);
   }
   __syncthreads();
-  // Jacobi sweeps.  One list of work units per round: the upper 2 x 2 blocks of the matrix, the
-  // planes of the next round, and (plane, row pair) updates of V^T; every thread takes units
-  // tid, tid + 1024, ...  V^T units: v = plane * nh + half-row, decoded with a multiply-shift
-  // (exact for v < 2^11 and nh <= 36: the rounding error of 2^20 / nh times v stays below 1 / nh).
-  const int nh = (n + 1) >> 1;
-  const int nunits = nblk + np + np * nh;
-  const unsigned vinv = (1u << 20) / (unsigned)nh + 1u;
+  // Jacobi sweeps.  Every round, the last pw warps compute the planes of the next round, three
+  // lanes per plane (a_uu, a_vv, a_uv of the rotated matrix, combined by shuffles), ten planes per
+  // warp; the other threads take the remaining work list: the upper 2 x 2 blocks of the matrix and
+  // (plane, six-column group) updates of V^T, units tid, tid + nthr_o, ...  V^T units:
+  // v = plane * nq + group, decoded with a multiply-shift (exact for v < 2^11 and nq <= 12: the
+  // rounding error of 2^20 / nq times v stays below 1 / nq).
+  const int nq = (n + 5) / 6;
+  const int pw = (np + 9) / 10;
+  const int nthr_o = SR_THREADS - 32 * pw;
+  const int nunits = nblk + np * nq;
+  const unsigned vinv = (1u << 20) / (unsigned)nq + 1u;
+  const bool plane_warp = warp >= SR_THREADS / 32 - pw;
+  const int pt = (warp - (SR_THREADS / 32 - pw)) * 10 + lane / 3;  // plane of this lane
+  const int pe = lane % 3;                                          // 0: a_uu, 1: a_vv, 2: a_uv
+  const int pbase = lane - pe;
   float2* Scur = B1;
   float2* Snxt = B0;
   int par = 0;
@@ -372,66 +381,82 @@ __global__ __launch_bounds__(SR_THREADS) void k_small_rr32(const float2* __restr
       Plane* nxt = pl + (par ^ 1) * 36;
       const int* icur = idx + par * SR_NMAX;
       int* inxt = idx + (par ^ 1) * SR_NMAX;
-      if (tid < npad) inxt[npos[tid]] = icur[tid];
-      for (int u = tid; u < nunits; u += SR_THREADS) {
-        if (u < nblk) {
-          const int bt = blk[u];
-          const int t1 = bt & 255, t2 = bt >> 8;
-          const Plane p1 = cur[t1], p2 = cur[t2];
-          const int a0 = 2 * t1, b0 = 2 * t2;
-          const int ra = npos[a0], rb = npos[a0 + 1];
-          const float4 r0 = *reinterpret_cast<const float4*>(Scur + a0 * SR_LD + b0);
-          const float4 r1 = *reinterpret_cast<const float4*>(Scur + (a0 + 1) * SR_LD + b0);
-          if (t1 == t2) {
-            const float2 m00 = make_float2(r0.x, r0.y), m01 = make_float2(r0.z, r0.w);
-            const float2 m10 = zconj(m01), m11 = make_float2(r1.z, r1.w);
-            const float2 y00 = col_rot(m00, m01, p2, 0), y10 = col_rot(m10, m11, p2, 0);
-            const float2 y01 = col_rot(m00, m01, p2, 1), y11 = col_rot(m10, m11, p2, 1);
-            const float2 e00 = row_rot(y00, y10, p1, 0), e11 = row_rot(y01, y11, p1, 1);
-            const float2 e01 = p1.on ? make_float2(0.f, 0.f) : row_rot(y01, y11, p1, 0);
-            Snxt[ra * SR_LD + ra] = make_float2(e00.x, 0.f);
-            Snxt[rb * SR_LD + rb] = make_float2(e11.x, 0.f);
-            const bool sw = ra > rb;
-            Snxt[(sw ? rb : ra) * SR_LD + (sw ? ra : rb)] = sw ? zconj(e01) : e01;
-          } else {
-            const int ca = npos[b0], cb = npos[b0 + 1];
-            const float2 m00 = make_float2(r0.x, r0.y), m01 = make_float2(r0.z, r0.w);
-            const float2 m10 = make_float2(r1.x, r1.y), m11 = make_float2(r1.z, r1.w);
-            const float2 y00 = col_rot(m00, m01, p2, 0), y10 = col_rot(m10, m11, p2, 0);
-            const float2 y01 = col_rot(m00, m01, p2, 1), y11 = col_rot(m10, m11, p2, 1);
-            const float2 e00 = row_rot(y00, y10, p1, 0), e01 = row_rot(y01, y11, p1, 0);
-            const float2 e10 = row_rot(y00, y10, p1, 1), e11 = row_rot(y01, y11, p1, 1);
-            bool sw;
-            sw = ra > ca; Snxt[(sw ? ca : ra) * SR_LD + (sw ? ra : ca)] = sw ? zconj(e00) : e00;
-            sw = ra > cb; Snxt[(sw ? cb : ra) * SR_LD + (sw ? ra : cb)] = sw ? zconj(e01) : e01;
-            sw = rb > ca; Snxt[(sw ? ca : rb) * SR_LD + (sw ? rb : ca)] = sw ? zconj(e10) : e10;
-            sw = rb > cb; Snxt[(sw ? cb : rb) * SR_LD + (sw ? rb : cb)] = sw ? zconj(e11) : e11;
-          }
-        } else if (u < nblk + np) {
-          // plane t of the next round: its positions come from u0, v0 of this round
-          const int t = u - nblk;
-          const int u0 = ppos[2 * t], v0 = ppos[2 * t + 1];
+      if (plane_warp) {
+        // plane pt of the next round: its positions come from u0, v0 of this round
+        const bool mine = lane < 30 && pt < np;
+        float2 e = make_float2(0.f, 0.f);
+        int u0 = 0, v0 = 0;
+        if (mine) {
+          u0 = ppos[2 * pt];
+          v0 = ppos[2 * pt + 1];
+          e = pe == 0 ? rotated_entry(Scur, cur, u0, u0)
+                      : (pe == 1 ? rotated_entry(Scur, cur, v0, v0) : rotated_entry(Scur, cur, u0, v0));
+        }
+        const float auu = __shfl_sync(0xffffffffu, e.x, pbase & 31);
+        const float avv = __shfl_sync(0xffffffffu, e.x, (pbase + 1) & 31);
+        const float2 auv = make_float2(__shfl_sync(0xffffffffu, e.x, (pbase + 2) & 31),
+                                       __shfl_sync(0xffffffffu, e.y, (pbase + 2) & 31));
+        if (mine && pe == 0) {
           const bool valid = icur[u0] >= 0 && icur[v0] >= 0;
-          const float2 auu = rotated_entry(Scur, cur, u0, u0), avv = rotated_entry(Scur, cur, v0, v0);
-          const float2 auv = rotated_entry(Scur, cur, u0, v0);
-          nxt[t] = make_plane(auu.x, avv.x, auv, floor_abs, valid);
-        } else {
-          const unsigned v = (unsigned)(u - nblk - np);
-          const int t = (int)((v * vinv) >> 20);
-          const int h = (int)v - t * nh;
-          const Plane w = cur[t];
-          if (w.on) {
-            // rows p, q of V^T, elements 2h and 2h + 1 (the second may be the padding column n)
-            float4* vp4 = reinterpret_cast<float4*>(Vt + icur[2 * t] * SR_LD + 2 * h);
-            float4* vq4 = reinterpret_cast<float4*>(Vt + icur[2 * t + 1] * SR_LD + 2 * h);
-            const float4 a = *vp4, b = *vq4;
-            const float2 sc = zconj(w.s);
-            const float2 p0 = zaxpy(w.c, make_float2(a.x, a.y), zneg(zmul(sc, make_float2(b.x, b.y))));
-            const float2 p1_ = zaxpy(w.c, make_float2(a.z, a.w), zneg(zmul(sc, make_float2(b.z, b.w))));
-            const float2 q0 = zaxpy(w.c, make_float2(b.x, b.y), zmul(w.s, make_float2(a.x, a.y)));
-            const float2 q1 = zaxpy(w.c, make_float2(b.z, b.w), zmul(w.s, make_float2(a.z, a.w)));
-            *vp4 = make_float4(p0.x, p0.y, p1_.x, p1_.y);
-            *vq4 = make_float4(q0.x, q0.y, q1.x, q1.y);
+          nxt[pt] = make_plane(auu, avv, auv, floor_abs, valid);
+        }
+      } else {
+        if (tid < npad) inxt[npos[tid]] = icur[tid];
+        for (int u = tid; u < nunits; u += nthr_o) {
+          if (u < nblk) {
+            const int bt = blk[u];
+            const int t1 = bt & 255, t2 = bt >> 8;
+            const Plane p1 = cur[t1], p2 = cur[t2];
+            const int a0 = 2 * t1, b0 = 2 * t2;
+            const int ra = npos[a0], rb = npos[a0 + 1];
+            const float4 r0 = *reinterpret_cast<const float4*>(Scur + a0 * SR_LD + b0);
+            const float4 r1 = *reinterpret_cast<const float4*>(Scur + (a0 + 1) * SR_LD + b0);
+            if (t1 == t2) {
+              const float2 m00 = make_float2(r0.x, r0.y), m01 = make_float2(r0.z, r0.w);
+              const float2 m10 = zconj(m01), m11 = make_float2(r1.z, r1.w);
+              const float2 y00 = col_rot(m00, m01, p2, 0), y10 = col_rot(m10, m11, p2, 0);
+              const float2 y01 = col_rot(m00, m01, p2, 1), y11 = col_rot(m10, m11, p2, 1);
+              const float2 e00 = row_rot(y00, y10, p1, 0), e11 = row_rot(y01, y11, p1, 1);
+              const float2 e01 = p1.on ? make_float2(0.f, 0.f) : row_rot(y01, y11, p1, 0);
+              Snxt[ra * SR_LD + ra] = make_float2(e00.x, 0.f);
+              Snxt[rb * SR_LD + rb] = make_float2(e11.x, 0.f);
+              const bool sw = ra > rb;
+              Snxt[(sw ? rb : ra) * SR_LD + (sw ? ra : rb)] = sw ? zconj(e01) : e01;
+            } else {
+              const int ca = npos[b0], cb = npos[b0 + 1];
+              const float2 m00 = make_float2(r0.x, r0.y), m01 = make_float2(r0.z, r0.w);
+              const float2 m10 = make_float2(r1.x, r1.y), m11 = make_float2(r1.z, r1.w);
+              const float2 y00 = col_rot(m00, m01, p2, 0), y10 = col_rot(m10, m11, p2, 0);
+              const float2 y01 = col_rot(m00, m01, p2, 1), y11 = col_rot(m10, m11, p2, 1);
+              const float2 e00 = row_rot(y00, y10, p1, 0), e01 = row_rot(y01, y11, p1, 0);
+              const float2 e10 = row_rot(y00, y10, p1, 1), e11 = row_rot(y01, y11, p1, 1);
+              bool sw;
+              sw = ra > ca; Snxt[(sw ? ca : ra) * SR_LD + (sw ? ra : ca)] = sw ? zconj(e00) : e00;
+              sw = ra > cb; Snxt[(sw ? cb : ra) * SR_LD + (sw ? ra : cb)] = sw ? zconj(e01) : e01;
+              sw = rb > ca; Snxt[(sw ? ca : rb) * SR_LD + (sw ? rb : ca)] = sw ? zconj(e10) : e10;
+              sw = rb > cb; Snxt[(sw ? cb : rb) * SR_LD + (sw ? rb : cb)] = sw ? zconj(e11) : e11;
+            }
+          } else {
+            const unsigned v = (unsigned)(u - nblk);
+            const int t = (int)((v * vinv) >> 20);
+            const int h = (int)v - t * nq;
+            const Plane w = cur[t];
+            if (w.on) {
+              // rows p, q of V^T, elements 6h .. 6h + 5 (columns n .. 71 are zero padding)
+              float4* vp4 = reinterpret_cast<float4*>(Vt + icur[2 * t] * SR_LD + 6 * h);
+              float4* vq4 = reinterpret_cast<float4*>(Vt + icur[2 * t + 1] * SR_LD + 6 * h);
+              const float2 sc = zconj(w.s);
+#pragma unroll
+              for (int g = 0; g < 3; ++g) {
+                const float4 a = vp4[g], b = vq4[g];
+                const float2 p0 = zaxpy(w.c, make_float2(a.x, a.y), zneg(zmul(sc, make_float2(b.x, b.y))));
+                const float2 p1_ = zaxpy(w.c, make_float2(a.z, a.w), zneg(zmul(sc, make_float2(b.z, b.w))));
+                const float2 q0 = zaxpy(w.c, make_float2(b.x, b.y), zmul(w.s, make_float2(a.x, a.y)));
+                const float2 q1 = zaxpy(w.c, make_float2(b.z, b.w), zmul(w.s, make_float2(a.z, a.w)));
+                vp4[g] = make_float4(p0.x, p0.y, p1_.x, p1_.y);
+                vq4[g] = make_float4(q0.x, q0.y, q1.x, q1.y);
+              }
+            }
           }
         }
       }
