@@ -27,6 +27,39 @@ __device__ __forceinline__ void kvec(const Geom& g, const double* Q, int k, int 
   K[2] = g.T[6] * a0 + g.T[7] * a1 + g.T[8] * a2;
 }
 
+// Wavevectors of a set of k-points in FP32, Kf[k N + q] = (K_0, K_1, K_2, 0) of plane wave q:
+// computed in FP64 by kvec and rounded, as the FP32 kernels would round them; they read the
+// table instead of recomputing (FP64 arithmetic and two integer divisions per element).
+__global__ void k_kvec_table(Geom g, const double* __restrict__ Q, int nk, float4* __restrict__ Kf) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nk * g.N) return;
+  const int k = (int)(t / g.N), q = (int)(t % g.N);
+  double K[3];
+  kvec(g, Q, k, q, K);
+  Kf[t] = make_float4((float)K[0], (float)K[1], (float)K[2], 0.f);
+}
+int launch_kvec_table(Geom g, const double* Q, int nk, float4* Kf, cudaStream_t s) {
+  const long long n = (long long)nk * g.N;
+  if (n == 0) return PC_OK;
+  k_kvec_table<<<cdiv(n, 256), 256, 0, s>>>(g, Q, nk, Kf);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+// The FP32 components of K at (k, q): from the table when there is one (FP32 data only).
+template <typename R>
+__device__ __forceinline__ void kvec_r(const Geom& g, const double* Q, const float4* Kf, int k, int q, R& k0, R& k1,
+                                       R& k2) {
+  if (Kf) {
+    const float4 kk = Kf[(long long)k * g.N + q];
+    k0 = (R)kk.x; k1 = (R)kk.y; k2 = (R)kk.z;
+  } else {
+    double K[3];
+    kvec(g, Q, k, q, K);
+    k0 = (R)K[0]; k1 = (R)K[1]; k2 = (R)K[2];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Complex GEMM on CUDA cores: C[col][p] = alpha * sum_q A[p][q] * B[col][q].
 // 64 x 64 output tile, 16-deep K slices staged in shared memory, 4 x 4 outputs per thread.
@@ -107,17 +140,17 @@ template int launch_gemm<float>(int, int, int, const float2*, int, const float2*
 // Strain stacks: E[s][vec][q] = sum_c B_s(K_q)[c] U[vec][c][q].
 template <typename R>
 __global__ void k_strain(const typename cplx_t<R>::type* __restrict__ X, int nvec, int m, Geom g,
-                         const double* __restrict__ Q, typename cplx_t<R>::type* __restrict__ E) {
+                         const double* __restrict__ Q, const float4* __restrict__ Kf,
+                         typename cplx_t<R>::type* __restrict__ E) {
   typedef typename cplx_t<R>::type C2;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int N = g.N;
   if (t >= (long long)nvec * N) return;
   int vec = (int)(t / N), q = (int)(t % N);
-  double K[3];
-  kvec(g, Q, vec / m, q, K);
+  R k0, k1, k2;
+  kvec_r<R>(g, Q, Kf, vec / m, q, k0, k1, k2);
   const C2* x = X + (long long)vec * 3 * N;
   C2 u0 = x[q], u1 = x[N + q], u2 = x[2 * N + q];
-  R k0 = (R)K[0], k1 = (R)K[1], k2 = (R)K[2];
   const long long st = (long long)nvec * N;
   C2* e = E + t;
   e[0]      = mk<R>((k0 * u0.x + k1 * u1.x + k2 * u2.x) * (R)RS3, (k0 * u0.y + k1 * u1.y + k2 * u2.y) * (R)RS3);
@@ -129,32 +162,33 @@ __global__ void k_strain(const typename cplx_t<R>::type* __restrict__ X, int nve
 }
 template <typename R>
 int launch_strain(const typename cplx_t<R>::type* X, int nvec, int m, Geom g, const double* Q,
-                  typename cplx_t<R>::type* E, cudaStream_t s) {
+                  typename cplx_t<R>::type* E, cudaStream_t s, const float4* Kf) {
   long long n = (long long)nvec * g.N;
-  k_strain<R><<<cdiv(n, 256), 256, 0, s>>>(X, nvec, m, g, Q, E);
+  if (sizeof(R) != sizeof(float)) Kf = nullptr;  // the table is FP32
+  k_strain<R><<<cdiv(n, 256), 256, 0, s>>>(X, nvec, m, g, Q, Kf, E);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
-template int launch_strain<double>(const double2*, int, int, Geom, const double*, double2*, cudaStream_t);
-template int launch_strain<float>(const float2*, int, int, Geom, const double*, float2*, cudaStream_t);
+template int launch_strain<double>(const double2*, int, int, Geom, const double*, double2*, cudaStream_t, const float4*);
+template int launch_strain<float>(const float2*, int, int, Geom, const double*, float2*, cudaStream_t, const float4*);
 
 // Epilogue: AX[vec][c][p] = sum_s c_s B_s(K_p)[c] Sig[s][vec][p]   (c_0 bulk, c_1 deviatoric).
 template <typename R>
 __global__ void k_epilogue(const typename cplx_t<R>::type* __restrict__ S, int nvec, int m, Geom g,
-                           const double* __restrict__ Q, R c0, R c1, typename cplx_t<R>::type* __restrict__ AX) {
+                           const double* __restrict__ Q, const float4* __restrict__ Kf, R c0, R c1,
+                           typename cplx_t<R>::type* __restrict__ AX) {
   typedef typename cplx_t<R>::type C2;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int N = g.N;
   if (t >= (long long)nvec * N) return;
   int vec = (int)(t / N), p = (int)(t % N);
-  double K[3];
-  kvec(g, Q, vec / m, p, K);
+  R k0, k1, k2;
+  kvec_r<R>(g, Q, Kf, vec / m, p, k0, k1, k2);
   const long long st = (long long)nvec * N;
   const C2* sg = S + t;
   C2 s0 = cscale(sg[0], c0 * (R)RS3);
   C2 s1 = cscale(sg[st], c1 * (R)RS2), s2 = cscale(sg[2 * st], c1 * (R)RS6);
   C2 s3 = cscale(sg[3 * st], c1 * (R)RS2), s4 = cscale(sg[4 * st], c1 * (R)RS2), s5 = cscale(sg[5 * st], c1 * (R)RS2);
-  R k0 = (R)K[0], k1 = (R)K[1], k2 = (R)K[2];
   C2* out = AX + (long long)vec * 3 * N + p;
   // component 1: B_0 = K1/sqrt3, B_1 = K1/sqrt2, B_2 = K1/sqrt6, B_4 = K3/sqrt2, B_5 = K2/sqrt2
   out[0] = mk<R>(k0 * (s0.x + s1.x + s2.x) + k2 * s4.x + k1 * s5.x, k0 * (s0.y + s1.y + s2.y) + k2 * s4.y + k1 * s5.y);
@@ -165,14 +199,15 @@ __global__ void k_epilogue(const typename cplx_t<R>::type* __restrict__ S, int n
 }
 template <typename R>
 int launch_epilogue(const typename cplx_t<R>::type* Sig, int nvec, int m, Geom g, const double* Q,
-                    R c0, R c1, typename cplx_t<R>::type* AX, cudaStream_t s) {
+                    R c0, R c1, typename cplx_t<R>::type* AX, cudaStream_t s, const float4* Kf) {
   long long n = (long long)nvec * g.N;
-  k_epilogue<R><<<cdiv(n, 256), 256, 0, s>>>(Sig, nvec, m, g, Q, c0, c1, AX);
+  if (sizeof(R) != sizeof(float)) Kf = nullptr;  // the table is FP32
+  k_epilogue<R><<<cdiv(n, 256), 256, 0, s>>>(Sig, nvec, m, g, Q, Kf, c0, c1, AX);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
-template int launch_epilogue<double>(const double2*, int, int, Geom, const double*, double, double, double2*, cudaStream_t);
-template int launch_epilogue<float>(const float2*, int, int, Geom, const double*, float, float, float2*, cudaStream_t);
+template int launch_epilogue<double>(const double2*, int, int, Geom, const double*, double, double, double2*, cudaStream_t, const float4*);
+template int launch_epilogue<float>(const float2*, int, int, Geom, const double*, float, float, float2*, cudaStream_t, const float4*);
 
 // ---------------------------------------------------------------------------
 // Relative residuals ||A x - lambda Omega x|| / (max(|lambda|, floor) ||Omega x||), one block per vector.
@@ -271,8 +306,8 @@ template int launch_resnorm<float>(const float2*, const float2*, const float*, i
 template <typename R>
 __global__ void k_precond(const typename cplx_t<R>::type* __restrict__ AX, const typename cplx_t<R>::type* __restrict__ OX,
                           const R* __restrict__ lam, const int* __restrict__ active, const int* __restrict__ kdone,
-                          int nvec, int m, int nb, Geom g, const double* __restrict__ Q, PrecRef pr,
-                          const double* __restrict__ chi_mean, typename cplx_t<R>::type* __restrict__ W) {
+                          int nvec, int m, int nb, Geom g, const double* __restrict__ Q, const float4* __restrict__ Kf,
+                          PrecRef pr, const double* __restrict__ chi_mean, typename cplx_t<R>::type* __restrict__ W) {
   typedef typename cplx_t<R>::type C2;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int N = g.N;
@@ -300,9 +335,8 @@ __global__ void k_precond(const typename cplx_t<R>::type* __restrict__ AX, const
   R sig = 0;
   for (int j = 0; j < nb; ++j) sig = fmax(sig, lam[k * m + j]);
   sig = fmax(sig, (R)1e-6) * (R)pr.shift_scale;
-  double Kd[3];
-  kvec(g, Q, k, q, Kd);
-  const R K0 = (R)Kd[0], K1 = (R)Kd[1], K2 = (R)Kd[2];
+  R K0, K1, K2;
+  kvec_r<R>(g, Q, Kf, k, q, K0, K1, K2);
   const R k2 = K0 * K0 + K1 * K1 + K2 * K2;
   const R a = (R)pr.two_pi_sq_V_over_sA * mu_r * k2 + (R)pr.half_lref_V_over_sA * rho_r * sig;
   const R b = (R)pr.two_pi_sq_V_over_sA * (lam_r + mu_r);
@@ -325,14 +359,15 @@ __global__ void k_precond(const typename cplx_t<R>::type* __restrict__ AX, const
 template <typename R>
 int launch_precond(const typename cplx_t<R>::type* AX, const typename cplx_t<R>::type* OX, const R* lam,
                    const int* active, const int* kdone, int nk, int m, int nb, Geom g, const double* Q, PrecRef pr,
-                   const double* chi_mean, typename cplx_t<R>::type* W, cudaStream_t s) {
+                   const double* chi_mean, typename cplx_t<R>::type* W, cudaStream_t s, const float4* Kf) {
   long long n = (long long)nk * m * g.N;
-  k_precond<R><<<cdiv(n, 256), 256, 0, s>>>(AX, OX, lam, active, kdone, nk * m, m, nb, g, Q, pr, chi_mean, W);
+  if (sizeof(R) != sizeof(float)) Kf = nullptr;  // the table is FP32
+  k_precond<R><<<cdiv(n, 256), 256, 0, s>>>(AX, OX, lam, active, kdone, nk * m, m, nb, g, Q, Kf, pr, chi_mean, W);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
-template int launch_precond<double>(const double2*, const double2*, const double*, const int*, const int*, int, int, int, Geom, const double*, PrecRef, const double*, double2*, cudaStream_t);
-template int launch_precond<float>(const float2*, const float2*, const float*, const int*, const int*, int, int, int, Geom, const double*, PrecRef, const double*, float2*, cudaStream_t);
+template int launch_precond<double>(const double2*, const double2*, const double*, const int*, const int*, int, int, int, Geom, const double*, PrecRef, const double*, double2*, cudaStream_t, const float4*);
+template int launch_precond<float>(const float2*, const float2*, const float*, const int*, const int*, int, int, int, Geom, const double*, PrecRef, const double*, float2*, cudaStream_t, const float4*);
 
 // ---------------------------------------------------------------------------
 // Initial block: the m lowest homogeneous plane waves (ranked by |K_q|, ties by index),

@@ -244,8 +244,8 @@ __global__ void k_tc_embed(const double2* __restrict__ W, int N, double scale, i
 // split bf16 K-major columns: E col = s * nvec + vec, X col = vec * 3 + c; K index 2q + {re, im}.
 // Slice t of E sits at E + t * es, of X at X + t * xs.
 __global__ void k_tc_split_strain(const float2* __restrict__ X, int nvec, int m, Geom g, const double* __restrict__ Q,
-                                  int Kp, __nv_bfloat16* __restrict__ E, long long es, __nv_bfloat16* __restrict__ Xs,
-                                  long long xs) {
+                                  const float4* __restrict__ Kf, int Kp, __nv_bfloat16* __restrict__ E, long long es,
+                                  __nv_bfloat16* __restrict__ Xs, long long xs) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int N = g.N;
   const int Kh = Kp / 2;  // complex slots per column (>= N)
@@ -256,13 +256,19 @@ __global__ void k_tc_split_strain(const float2* __restrict__ X, int nvec, int m,
   if (q < N) {
     const float2* x = X + (long long)vec * 3 * N;
     u0 = x[q]; u1 = x[N + q]; u2 = x[2 * N + q];
-    int M2 = 2 * g.M + 1, k = vec / m;
-    double a0 = Q[3 * k] + (double)(q / (M2 * M2) - g.M);
-    double a1 = Q[3 * k + 1] + (double)((q / M2) % M2 - g.M);
-    double a2 = Q[3 * k + 2] + (double)(q % M2 - g.M);
-    k0 = (float)(g.T[0] * a0 + g.T[1] * a1 + g.T[2] * a2);
-    k1 = (float)(g.T[3] * a0 + g.T[4] * a1 + g.T[5] * a2);
-    k2 = (float)(g.T[6] * a0 + g.T[7] * a1 + g.T[8] * a2);
+    const int k = vec / m;
+    if (Kf) {  // the k-set's FP32 wavevectors
+      const float4 kk = Kf[(long long)k * N + q];
+      k0 = kk.x; k1 = kk.y; k2 = kk.z;
+    } else {
+      int M2 = 2 * g.M + 1;
+      double a0 = Q[3 * k] + (double)(q / (M2 * M2) - g.M);
+      double a1 = Q[3 * k + 1] + (double)((q / M2) % M2 - g.M);
+      double a2 = Q[3 * k + 2] + (double)(q % M2 - g.M);
+      k0 = (float)(g.T[0] * a0 + g.T[1] * a1 + g.T[2] * a2);
+      k1 = (float)(g.T[3] * a0 + g.T[4] * a1 + g.T[5] * a2);
+      k2 = (float)(g.T[6] * a0 + g.T[7] * a1 + g.T[8] * a2);
+    }
   }
   float2 e[6];
   e[0] = make_float2((k0 * u0.x + k1 * u1.x + k2 * u2.x) * RS3, (k0 * u0.y + k1 * u1.y + k2 * u2.y) * RS3);
@@ -459,18 +465,18 @@ static int launch_tc_gemm(TcPlan* p, int which_A, const CUtensorMap* b, int col_
 }
 
 int tc_apply(TcPlan* p, const float2* X, float2* AX, float2* OX, int nvec, int m, Geom g, const double* Q,
-             cudaStream_t s) {
+             cudaStream_t s, const float4* Kf) {
   if (!tc_available(p) || nvec > p->nvec_max) return PC_EINVAL;
   const long long n = (long long)nvec * (p->Kp / 2);
   const long long es = (long long)6 * p->nvec_max * p->Kp, xs = (long long)3 * p->nvec_max * p->Kp;
-  k_tc_split_strain<<<cdiv(n, 256), 256, 0, s>>>(X, nvec, m, g, Q, p->Kp, p->E, es, p->X, xs);
+  k_tc_split_strain<<<cdiv(n, 256), 256, 0, s>>>(X, nvec, m, g, Q, Kf, p->Kp, p->E, es, p->X, xs);
   PC_LAUNCH_CHECK();
   // E column s * nvec + v holds stack s of vector v (the maps span the plan's capacity).
   int rc = launch_tc_gemm(p, 0, p->mE, 0, nvec, (float*)p->S, s);
   if (rc) return rc;
   rc = launch_tc_gemm(p, 1, p->mE, nvec, 5 * nvec, (float*)p->S, s);
   if (rc) return rc;
-  rc = launch_epilogue<float>(p->S, nvec, m, g, Q, 1.0f, 1.0f, AX, s);
+  rc = launch_epilogue<float>(p->S, nvec, m, g, Q, 1.0f, 1.0f, AX, s, Kf);
   if (rc) return rc;
   return launch_tc_gemm(p, 2, p->mX, 0, 3 * nvec, (float*)OX, s);
 }

@@ -14,7 +14,8 @@ bool tc_available(const TcPlan* p);
 // tensor-core operands: W * w_scale and T_rho * t_scale.
 int tc_prepare_operators(TcPlan* p, const double2* W, const double2* T, double w_scale, double t_scale, cudaStream_t s);
 // AX, OX for nvec FP32 vectors (vector v at k = v / m).
-int tc_apply(TcPlan* p, const float2* X, float2* AX, float2* OX, int nvec, int m, Geom g, const double* Q, cudaStream_t s);
+int tc_apply(TcPlan* p, const float2* X, float2* AX, float2* OX, int nvec, int m, Geom g, const double* Q, cudaStream_t s,
+             const float4* Kf = nullptr);
 
 // FP64-accurate operator products by exact 6-bit slicing on the tensor cores (oz_gemm.cu), for
 // the mixed form's final Rayleigh-Ritz step.  Eligible for 2N (padded to 32) below 2048.

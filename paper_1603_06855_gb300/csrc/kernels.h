@@ -53,10 +53,13 @@ int launch_gemm(int Mrows, int ncols, int K, const typename cplx_t<R>::type* A, 
 // Operator pieces.  Vector blocks are [vec][3][N] complex, vec = k*m + j.
 template <typename R>
 int launch_strain(const typename cplx_t<R>::type* X, int nvec, int m, Geom g, const double* Q,
-                  typename cplx_t<R>::type* E, cudaStream_t s);
+                  typename cplx_t<R>::type* E, cudaStream_t s, const float4* Kf = nullptr);
 template <typename R>
 int launch_epilogue(const typename cplx_t<R>::type* Sig, int nvec, int m, Geom g, const double* Q,
-                    R c0, R c1, typename cplx_t<R>::type* AX, cudaStream_t s);
+                    R c0, R c1, typename cplx_t<R>::type* AX, cudaStream_t s, const float4* Kf = nullptr);
+// Kf[k N + q] = FP32 wavevector (K_0, K_1, K_2, 0) of plane wave q at the k-th point of Q (nk points);
+// the FP32 kernels above and below read it when given (it is ignored for FP64 data).
+int launch_kvec_table(Geom g, const double* Q, int nk, float4* Kf, cudaStream_t s);
 
 struct PrecConsts {
   double c_mu;    // (2pi)^2 V mu_ref / sA ... multiplied by |K|^2
@@ -79,7 +82,8 @@ int launch_resnorm(const typename cplx_t<R>::type* AX, const typename cplx_t<R>:
 template <typename R>
 int launch_precond(const typename cplx_t<R>::type* AX, const typename cplx_t<R>::type* OX,
                    const R* lam, const int* active, const int* kdone, int nk, int m, int nb, Geom g,
-                   const double* Q, PrecRef pr, const double* chi_mean, typename cplx_t<R>::type* W, cudaStream_t s);
+                   const double* Q, PrecRef pr, const double* chi_mean, typename cplx_t<R>::type* W, cudaStream_t s,
+                   const float4* Kf = nullptr);
 template <typename R>
 int launch_init_guess(typename cplx_t<R>::type* X, int nk, int m, Geom g, const double* Q, unsigned long long seed,
                       cudaStream_t s);

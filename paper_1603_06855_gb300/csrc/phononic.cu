@@ -86,7 +86,8 @@ struct pc_ctx {
   double *weights = nullptr;
   int *pairs = nullptr, *npairs = nullptr;
   double2* adj_t2 = nullptr;
-  double* adj_part = nullptr;  // chunk sums of the adjoint's reduction
+  double* adj_part = nullptr;
+  float4* Kf = nullptr;  // FP32 wavevectors of the k-points, [k][N] (mixed form)  // chunk sums of the adjoint's reduction
   TcPlan* tc = nullptr;
   TcPlan* tcg[kMaxGroups] = {};  // workspaces of k groups 1.. (operators shared with tc)
   OzPlan* oz = nullptr;          // sliced FP64-accurate operators of the final Rayleigh-Ritz step (mixed form)
@@ -237,7 +238,7 @@ static void free_kset(pc_ctx* c) {
   dfree(c->Xd); dfree(c->AXd); dfree(c->OXd); dfree(c->Ed); dfree(c->Sd); dfree(c->Th); dfree(c->St);
   dfree(c->gpartd); dfree(c->GAd); dfree(c->GOd); dfree(c->Cd);
   dfree(c->lamd); dfree(c->lam_nd); dfree(c->rnormd); dfree(c->actived);
-  dfree(c->weights); dfree(c->pairs); dfree(c->npairs); dfree(c->adj_t2); dfree(c->adj_part);
+  dfree(c->weights); dfree(c->pairs); dfree(c->npairs); dfree(c->adj_t2); dfree(c->adj_part); dfree(c->Kf);
   for (auto& t : c->tcg)
     if (t) { tc_plan_destroy(t); t = nullptr; }
   if (c->tc) { tc_plan_destroy(c->tc); c->tc = nullptr; }
@@ -429,6 +430,7 @@ extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
   const size_t rsz = (c->prm.precision == PC_FP64) ? sizeof(double) : sizeof(float);
   int rc = PC_OK;
   rc |= dalloc(&c->Q, 3 * (size_t)nk);
+  if (c->prm.precision == PC_MIXED) rc |= dalloc(&c->Kf, (size_t)nk * N);
   for (auto& b : c->blk)
     if (cudaMalloc(&b, nvec * n3 * esz) != cudaSuccess) { b = nullptr; rc = PC_ENOMEM; }
   if (cudaMalloc(&c->E, 6 * nvec * N * esz) != cudaSuccess) { c->E = nullptr; rc = PC_ENOMEM; }
@@ -495,6 +497,10 @@ extern "C" int pc_set_kpoints(pc_ctx* c, const double* q, int nk) {
   }
   if (rc != PC_OK) { free_kset(c); return PC_ENOMEM; }
   if (cudaMemcpy(c->Q, q, 3 * sizeof(double) * nk, cudaMemcpyHostToDevice) != cudaSuccess) {
+    free_kset(c);
+    return PC_ECUDA;
+  }
+  if (c->Kf && (launch_kvec_table(c->geom, c->Q, nk, c->Kf, 0) != PC_OK || cudaStreamSynchronize(0) != cudaSuccess)) {
     free_kset(c);
     return PC_ECUDA;
   }
@@ -610,10 +616,12 @@ static int apply_sliced(pc_ctx* c, OzPlan* oz, const double2* X, double2* AX, do
   return launch_epilogue<double>(S, nvec, m, c->geom, Q, epi, epi, AX, s);
 }
 
-// Nondimensional A' X and Omega' X for FP32 vectors (vector v at k = v / m of Q): the split-BF16
+// Nondimensional A' X and Omega' X for FP32 vectors (vector v at k-point k0 + v / m): the split-BF16
 // tensor-core path; the FP32 CUDA-core GEMM only where the tensor-core plan could not be set up.
-static int apply_fp32(pc_ctx* c, const float2* X, float2* AX, float2* OX, int nvec, int m, const double* Q,
+static int apply_fp32(pc_ctx* c, const float2* X, float2* AX, float2* OX, int nvec, int m, int k0,
                       cudaStream_t s, TcPlan* plan = nullptr) {
+  const double* Q = c->Q + 3LL * k0;
+  const float4* Kf = c->Kf ? c->Kf + (long long)k0 * c->N : nullptr;
   if (!plan) plan = c->tc;
   if (plan && tc_available(plan)) {
     if (!c->tc_ready) {
@@ -621,19 +629,19 @@ static int apply_fp32(pc_ctx* c, const float2* X, float2* AX, float2* OX, int nv
       if (rc) return rc;
       c->tc_ready = true;
     }
-    return tc_apply(plan, X, AX, OX, nvec, m, c->geom, Q, s);
+    return tc_apply(plan, X, AX, OX, nvec, m, c->geom, Q, s, Kf);
   }
   const int N = c->N;
   const long long NN = (long long)N * N;
   float2* E = (float2*)c->E;
   float2* S = (float2*)c->S;
-  int rc = launch_strain<float>(X, nvec, m, c->geom, Q, E, s);
+  int rc = launch_strain<float>(X, nvec, m, c->geom, Q, E, s, Kf);
   if (rc) return rc;
   rc = launch_gemm<float>(N, nvec, N, c->Wf, N, E, N, S, N, 1.0f, s);
   if (rc) return rc;
   rc = launch_gemm<float>(N, 5 * nvec, N, c->Wf + NN, N, E + (long long)nvec * N, N, S + (long long)nvec * N, N, 1.0f, s);
   if (rc) return rc;
-  rc = launch_epilogue<float>(S, nvec, m, c->geom, Q, 1.0f, 1.0f, AX, s);
+  rc = launch_epilogue<float>(S, nvec, m, c->geom, Q, 1.0f, 1.0f, AX, s, Kf);
   if (rc) return rc;
   return launch_gemm<float>(N, 3 * nvec, N, c->Tf, N, X, N, OX, N, 1.0f, s);
 }
@@ -659,7 +667,7 @@ int apply_R<double>(pc_ctx* c, const KSet& ks, const double2* X, double2* AX, do
 }
 template <>
 int apply_R<float>(pc_ctx* c, const KSet& ks, const float2* X, float2* AX, float2* OX) {
-  return apply_fp32(c, X, AX, OX, ks.nk * c->m, c->m, c->Q + 3 * ks.k0, ks.s, ks.tc);
+  return apply_fp32(c, X, AX, OX, ks.nk * c->m, c->m, ks.k0, ks.s, ks.tc);
 }
 
 template <typename R>
@@ -838,7 +846,8 @@ static int run_block_iteration(pc_ctx* c, KSet& ks) {
     }
     ph_end(c, idle_slot, s);
     if (ks.unconv == 0) break;
-    TRY(launch_precond<R>(AX, OX, lam, active, kdone, nk, m, nb, c->geom, Qk, c->pr, c->chi_mean, Wb, s));
+    TRY(launch_precond<R>(AX, OX, lam, active, kdone, nk, m, nb, c->geom, Qk, c->pr, c->chi_mean, Wb, s,
+                          c->Kf ? c->Kf + (long long)k0 * c->N : nullptr));
     // W <- W - X (OX^H W) - P (OP^H W), before the operator is applied
     {
       const int nproj = hasP ? 2 : 1;
@@ -1341,7 +1350,7 @@ extern "C" int pc_apply_operator(pc_ctx* c, int k, int ncols, const double* x, d
     float2* af = (float2*)c->blk[4];
     float2* of = (float2*)c->blk[5];
     int rc = launch_d2f((const double2*)x, xf, n, 1.0, s);
-    if (!rc) rc = apply_fp32(c, xf, af, of, ncols, ncols, c->Q + 3LL * k, s);
+    if (!rc) rc = apply_fp32(c, xf, af, of, ncols, ncols, k, s);
     if (!rc) rc = launch_convert_f2d(af, (double2*)ax, n, s);
     if (!rc) rc = launch_convert_f2d(of, (double2*)ox, n, s);
     if (!rc) rc = launch_scale_d2((double2*)ax, n, c->sA, s);
