@@ -309,6 +309,24 @@ __global__ void k_precond(const typename cplx_t<R>::type* __restrict__ AX, const
                           int nvec, int m, int nb, Geom g, const double* __restrict__ Q, const float4* __restrict__ Kf,
                           PrecRef pr, const double* __restrict__ chi_mean, typename cplx_t<R>::type* __restrict__ W) {
   typedef typename cplx_t<R>::type C2;
+  // the reference medium (Lame constants and density at the mean chi), once per block in FP64
+  __shared__ R ref[3];
+  if (threadIdx.x == 0) {
+    const double cm = *chi_mean;
+    double lam_d, mu_d;
+    if (pr.ref_mode == 1) {  // compliance linear in chi: bulk 1/(3 f1), shear 1/(2 f2)
+      const double f1 = pr.f1_0 + cm * (pr.f1_1 - pr.f1_0), f2 = pr.f2_0 + cm * (pr.f2_1 - pr.f2_0);
+      mu_d = 0.5 / f2;
+      lam_d = 1.0 / (3.0 * f1) - 2.0 * mu_d / 3.0;
+    } else {
+      lam_d = pr.lam0 + cm * (pr.lam1 - pr.lam0);
+      mu_d = pr.mu0 + cm * (pr.mu1 - pr.mu0);
+    }
+    ref[0] = (R)lam_d;
+    ref[1] = (R)mu_d;
+    ref[2] = (R)(pr.rho0 + cm * (pr.rho1 - pr.rho0));
+  }
+  __syncthreads();
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int N = g.N;
   if (t >= (long long)nvec * N) return;
@@ -319,19 +337,9 @@ __global__ void k_precond(const typename cplx_t<R>::type* __restrict__ AX, const
     w[0] = mk<R>(0, 0); w[N] = mk<R>(0, 0); w[2 * N] = mk<R>(0, 0);
     return;
   }
-  const double cm = *chi_mean;
-  double lam_d, mu_d;
-  if (pr.ref_mode == 1) {  // compliance linear in chi: bulk 1/(3 f1), shear 1/(2 f2)
-    const double f1 = pr.f1_0 + cm * (pr.f1_1 - pr.f1_0), f2 = pr.f2_0 + cm * (pr.f2_1 - pr.f2_0);
-    mu_d = 0.5 / f2;
-    lam_d = 1.0 / (3.0 * f1) - 2.0 * mu_d / 3.0;
-  } else {
-    lam_d = pr.lam0 + cm * (pr.lam1 - pr.lam0);
-    mu_d = pr.mu0 + cm * (pr.mu1 - pr.mu0);
-  }
-  const R lam_r = (R)lam_d;
-  const R mu_r = (R)mu_d;
-  const R rho_r = (R)(pr.rho0 + cm * (pr.rho1 - pr.rho0));
+  const R lam_r = ref[0];
+  const R mu_r = ref[1];
+  const R rho_r = ref[2];
   R sig = 0;
   for (int j = 0; j < nb; ++j) sig = fmax(sig, lam[k * m + j]);
   sig = fmax(sig, (R)1e-6) * (R)pr.shift_scale;
