@@ -124,10 +124,12 @@ int launch_small_rr(const typename cplx_t<R>::type* GA, const typename cplx_t<R>
                     int nk, R drop_tol, const int* kdone, R* lam_out, typename cplx_t<R>::type* coef, int* status,
                     cudaStream_t s);
 // The FP32 projected problems of the mixed form (small_rr.cu): same contract as
-// launch_small_rr<float>; when flops is given, the algorithmic flops of every problem solved are
-// added to it (device counter).
+// launch_small_rr<float>; when cp is given, the conjugate-direction coefficients of
+// launch_small_pdir<float> (absolute drop level pdir_abs) are computed by the same CTAs; when
+// flops is given, the algorithmic flops of every problem solved are added to it (device counter).
 int launch_small_rr32(const float2* GA, const float2* GO, int n, int m, int nk, float drop_tol, const int* kdone,
-                      float* lam_out, float2* coef, int* status, double* flops, cudaStream_t s);
+                      float* lam_out, float2* coef, float2* cp, float pdir_abs, int* status, double* flops,
+                      cudaStream_t s);
 // Cholesky-QR transform of the Gram G (m x m per k).  When Gref is given (rows_ref x m per
 // k, scale -1, its last m rows holding -Y^H Omega Y before projection), a column whose
 // Omega-norm^2 after projection is below rel_tol times the one before is dropped.

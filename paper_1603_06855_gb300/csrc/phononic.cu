@@ -705,12 +705,13 @@ template <typename R>
 static int small_rr_any(pc_ctx* c, int nk, const typename Ops<R>::C2* GA, const typename Ops<R>::C2* GO, int n, int m,
                         const int* kdone, R* lam, typename Ops<R>::C2* cX, typename Ops<R>::C2* cP, cudaStream_t s) {
   int rc;
-  if constexpr (std::is_same<R, float>::value)
-    rc = launch_small_rr32(GA, GO, n, m, nk, Ops<R>::drop_small, kdone, lam, cX, c->status,
-                           c->profiling ? c->small_flops : nullptr, s);
-  else
+  if constexpr (std::is_same<R, float>::value) {  // the conjugate directions from the same CTAs
+    rc = launch_small_rr32(GA, GO, n, m, nk, Ops<R>::drop_small, kdone, lam, cX, cP, SmallTol<R>::pdir_abs,
+                           c->status, c->profiling ? c->small_flops : nullptr, s);
+  } else {
     rc = launch_small_rr<R>(GA, GO, n, m, nk, Ops<R>::drop_small, kdone, lam, cX, c->status, s);
-  if (!rc && cP) rc = launch_small_pdir<R>(GO, cX, n, m, nk, kdone, SmallTol<R>::pdir_abs, cP, s);
+    if (!rc && cP) rc = launch_small_pdir<R>(GO, cX, n, m, nk, kdone, SmallTol<R>::pdir_abs, cP, s);
+  }
   return rc;
 }
 template <typename R>

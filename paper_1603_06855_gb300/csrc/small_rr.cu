@@ -23,10 +23,13 @@
 //     eps max_{i < m} |a_ii| (the absolute floor is the rounding level of the current Ritz
 //     block); after each sweep one pass over all pairs ends the iteration when none would
 //     rotate.
-//  5. the lowest m eigenvalues of the kept coordinates and their coefficients D V.
+//  5. the lowest m eigenvalues of the kept coordinates and their coefficients D V;
+//  6. when asked, the conjugate-direction coefficients of the next iteration from the same
+//     CTA (pdir32: Cholesky-QR of the part of the old Ritz block outside the new one).
 // This is the mixed form's version (FP32, four 72 x 74 complex matrices in shared memory);
 // the FP64 form keeps the kernel in lobpcg.cu.
 #include "kernels.h"
+#include "small_dense.cuh"
 
 namespace {
 
@@ -176,12 +179,87 @@ __device__ __forceinline__ void block_forward(const float2* L, float2* const P[2
   }
 }
 
+// Conjugate-direction coefficients, inside the CTA that solved the projected problem.  With the
+// Ritz coefficients cX (n x m, cX^H GO cX = I) of the basis S = [X_old, W, P_old], the next
+// conjugate block spans the part of span(X_old) that is GO-orthogonal to the new Ritz block:
+// Z = E - cX (cX^H GO E), E = [I_m; 0], orthonormalised in the GO metric (H = Z^H GO Z,
+// unit-diagonal scaled, Cholesky-QR; columns with H_jj at or below abs_drop carry only rounding
+// and are dropped), cP = Z T.  go: the projected Gram matrix (global); G (stride SR_LD), cx, z, gz
+// (n x m compact), Mm (m x m), tmp (m), Dd (m), drp (m): shared workspaces; cp: output (n x m).
+__device__ void pdir32(const float2* __restrict__ go, int n, int m, float abs_drop, float2* G, const float2* cx,
+                       float2* z, float2* gz, float2* Mm, float2* tmp, float* Dd, int* drp, float2* __restrict__ cp) {
+  const int tid = threadIdx.x;
+  for (int t = tid; t < n * n; t += SR_THREADS) {  // GO, symmetrised
+    const int r = t / n, q = t - (t / n) * n;
+    const float2 g1 = go[r * n + q], g2 = go[q * n + r];
+    G[r * SR_LD + q] = make_float2(0.5f * (g1.x + g2.x), 0.5f * (g1.y - g2.y));
+  }
+  __syncthreads();
+  for (int t = tid; t < m * m; t += SR_THREADS) {  // M = cX^H GO E
+    const int i = t / m, j = t - (t / m) * m;
+    float2 s = make_float2(0.f, 0.f);
+    for (int r = 0; r < n; ++r) cfmac(s, cx[r * m + i], G[r * SR_LD + j]);
+    Mm[t] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < n * m; t += SR_THREADS) {  // Z = E - cX M
+    const int r = t / m, j = t - (t / m) * m;
+    float2 s = make_float2(r == j ? 1.f : 0.f, 0.f);
+    for (int i = 0; i < m; ++i) {
+      const float2 v = cmul(cx[r * m + i], Mm[i * m + j]);
+      s.x -= v.x;
+      s.y -= v.y;
+    }
+    z[t] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < n * m; t += SR_THREADS) {  // GZ = GO Z
+    const int r = t / m, j = t - (t / m) * m;
+    float2 s = make_float2(0.f, 0.f);
+    for (int q = 0; q < n; ++q) cfma(s, G[r * SR_LD + q], z[q * m + j]);
+    gz[t] = s;
+  }
+  __syncthreads();
+  for (int i = tid; i < m; i += SR_THREADS) {  // column scales of H = Z^H GZ
+    float2 s = make_float2(0.f, 0.f);
+    for (int r = 0; r < n; ++r) cfmac(s, z[r * m + i], gz[r * m + i]);
+    Dd[i] = (s.x > abs_drop && s.x == s.x) ? 1.f / sqrtf(s.x) : 0.f;
+    drp[i] = 0;
+  }
+  __syncthreads();
+  for (int t = tid; t < m * m; t += SR_THREADS) {  // H, unit-diagonal scaled and symmetrised
+    const int i = t / m, j = t - (t / m) * m;
+    float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
+    for (int r = 0; r < n; ++r) {
+      cfmac(s1, z[r * m + i], gz[r * m + j]);
+      cfmac(s2, z[r * m + j], gz[r * m + i]);
+    }
+    const float sc = Dd[i] * Dd[j] * 0.5f;
+    Mm[t] = make_float2((s1.x + s2.x) * sc, (s1.y - s2.y) * sc);
+  }
+  __syncthreads();
+  chol_drop<float>(Mm, m, m, 1e-10f, drp);
+  tri_inv_lower<float>(Mm, m, m, tmp);
+  for (int t = tid; t < n * m; t += SR_THREADS) {  // cP = Z T, T[i][c] = D_i conj(Li[c][i]) for c >= i
+    const int r = t / m, c = t - (t / m) * m;
+    float2 s = make_float2(0.f, 0.f);
+    if (!drp[c] && Dd[c] != 0.f) {
+      for (int i = 0; i <= c; ++i) {
+        const float2 li = Mm[c * m + i];
+        cfma(s, z[r * m + i], make_float2(li.x * Dd[i], -li.y * Dd[i]));
+      }
+    }
+    cp[t] = s;
+  }
+}
+
 }  // namespace
 
 __global__ __launch_bounds__(SR_THREADS) void k_small_rr32(const float2* __restrict__ GA, const float2* __restrict__ GO,
                                                          int n, int m, float drop_tol, const int* __restrict__ kdone,
                                                          float* __restrict__ lam_out, float2* __restrict__ coef,
-                                                         int* status, double* flops) {
+                                                         float2* __restrict__ cpo, float pdir_abs, int* status,
+                                                         double* flops) {
   extern __shared__ __align__(16) unsigned char smem[];
   float2* B0 = (float2*)smem;          // GO -> L -> Jacobi buffer 1
   float2* B1 = B0 + SR_MAT;            // GA -> T = L^-1 GA -> Jacobi buffer 0
@@ -203,10 +281,12 @@ __global__ __launch_bounds__(SR_THREADS) void k_small_rr32(const float2* __restr
   const float2* ga = GA + (long long)k * n * n;
   const float2* go = GO + (long long)k * n * n;
   float2* ck = coef + (long long)k * n * m;
-  if (kdone && kdone[k]) {  // locked k-point: keep its block, leave lambda untouched
+  float2* cpk = cpo ? cpo + (long long)k * n * m : nullptr;  // conjugate-direction coefficients (or none)
+  if (kdone && kdone[k]) {  // locked k-point: keep its block, leave lambda untouched, no conjugate block
     for (int t = tid; t < n * m; t += blockDim.x) {
       const int i = t / m, j = t % m;
       ck[t] = make_float2(i == j ? 1.f : 0.f, 0.f);
+      if (cpk) cpk[t] = make_float2(0.f, 0.f);
     }
     return;
   }
@@ -317,6 +397,14 @@ __global__ __launch_bounds__(SR_THREADS) void k_small_rr32(const float2* __restr
     }
     for (int j = tid; j < m; j += blockDim.x) lam_out[(long long)k * m + j] = ga[j * n + j].x / go[j * n + j].x;
     if (tid == 0) set_status(status, PC_ENOCONV);
+    if (cpk) {
+      for (int t = tid; t < n * m; t += blockDim.x) {
+        const int i = t / m, j = t % m;
+        B1[t] = make_float2(i == j ? 1.f : 0.f, 0.f);
+      }
+      __syncthreads();
+      pdir32(go, n, m, pdir_abs, B0, B1, B1 + n * m, B1 + 2 * n * m, Cm, Cm + m * m, ev, drop, cpk);
+    }
     return;
   }
   const int npad = nk_ + (nk_ & 1), np = npad / 2, nrounds = npad - 1;
@@ -496,9 +584,15 @@ __global__ __launch_bounds__(SR_THREADS) void k_small_rr32(const float2* __restr
   for (int t = tid; t < n * m; t += blockDim.x) {
     const int i = t / m, j = t % m;
     const float2 v = Vt[icur[perm[j]] * SR_LD + i];  // V[i][col] = V^T[col][i]
-    ck[t] = make_float2(v.x * D[i], v.y * D[i]);
+    const float2 c = make_float2(v.x * D[i], v.y * D[i]);
+    ck[t] = c;
+    B1[t] = c;  // the Jacobi buffers are free: cX for the conjugate directions
   }
   for (int j = tid; j < m; j += blockDim.x) lam_out[(long long)k * m + j] = ev[perm[j]];
+  if (cpk) {
+    __syncthreads();
+    pdir32(go, n, m, pdir_abs, B0, B1, B1 + n * m, B1 + 2 * n * m, Cm, Cm + m * m, ev, drop, cpk);
+  }
   if (flops && tid == 0) {
     // algorithmic work: Cholesky n^3/6, L^-1 GA n^3/2, L^-1 T^H n^3/2 and L^-1 n^3/6 complex
     // multiply-adds (8 real flops each); per Jacobi sweep n_k (n_k - 1) / 2 rotations, each
@@ -509,14 +603,15 @@ __global__ __launch_bounds__(SR_THREADS) void k_small_rr32(const float2* __restr
 }
 
 int launch_small_rr32(const float2* GA, const float2* GO, int n, int m, int nk, float drop_tol, const int* kdone,
-                      float* lam_out, float2* coef, int* status, double* flops, cudaStream_t s) {
+                      float* lam_out, float2* coef, float2* cp, float pdir_abs, int* status, double* flops,
+                      cudaStream_t s) {
   if (n > SR_NMAX || m > n || n < 1) return PC_EINVAL;
   const size_t sm = sizeof(float2) * 4 * (size_t)SR_MAT + sizeof(Plane) * 72 + sizeof(float) * 2 * SR_NMAX +
                     sizeof(int) * (7 * SR_NMAX + SR_BLK + 8);
   static const cudaError_t attr =  // once, thread-safe (k groups launch from several host threads)
       cudaFuncSetAttribute(k_small_rr32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   (void)attr;
-  k_small_rr32<<<nk, SR_THREADS, sm, s>>>(GA, GO, n, m, drop_tol, kdone, lam_out, coef, status, flops);
+  k_small_rr32<<<nk, SR_THREADS, sm, s>>>(GA, GO, n, m, drop_tol, kdone, lam_out, coef, cp, pdir_abs, status, flops);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
