@@ -150,7 +150,8 @@ __global__ void k_toeplitz(const double2* __restrict__ sf, int M, double V, doub
 __global__ void k_gj_pivot(const double2* __restrict__ A, int N, long long mstride, int k0, int bb,
                            double2* __restrict__ Pbuf, double2* __restrict__ Ar) {
   __shared__ double2 P[GJ_B * (GJ_B + 1)];
-  __shared__ double2 prow[GJ_B], pcol[GJ_B];
+  __shared__ double2 prow[GJ_B], pcol[GJ_B], qrow[GJ_B];
+  __shared__ double2 sip;
   const int z = blockIdx.z;
   const double2* Az = A + z * mstride;
   const int ld = GJ_B + 1;
@@ -165,22 +166,30 @@ __global__ void k_gj_pivot(const double2* __restrict__ A, int N, long long mstri
     arz[(long long)r * N + c] = Az[(long long)(k0 + r) * N + c];
   }
   __syncthreads();
+  // One scalar step per pivot k.  The reciprocal of the pivot and the scaled pivot row
+  // q_c = prow_c / piv are formed once (FP64 division and complex products are scarce on one SM's
+  // FP64 pipe), then every element takes its update.
   for (int k = 0; k < bb; ++k) {
     if ((int)threadIdx.x < bb) {
       prow[threadIdx.x] = P[k * ld + threadIdx.x];
       pcol[threadIdx.x] = P[threadIdx.x * ld + k];
     }
+    if (threadIdx.x == 0) {
+      const double2 piv = P[k * ld + k];
+      const double den = piv.x * piv.x + piv.y * piv.y;
+      sip = make_double2(piv.x / den, -piv.y / den);
+    }
     __syncthreads();
-    const double2 piv = prow[k];
-    const double den = piv.x * piv.x + piv.y * piv.y;
-    const double2 ip = make_double2(piv.x / den, -piv.y / den);
+    const double2 ip = sip;
+    if ((int)threadIdx.x < bb) qrow[threadIdx.x] = cmul(prow[threadIdx.x], ip);
+    __syncthreads();
     for (int t = threadIdx.x; t < bb * bb; t += blockDim.x) {
       int r = t / bb, c = t % bb;
       double2 v;
       if (r == k && c == k) v = ip;
-      else if (r == k) v = cmul(prow[c], ip);
+      else if (r == k) v = qrow[c];
       else if (c == k) v = cmul(make_double2(-pcol[r].x, -pcol[r].y), ip);
-      else v = csub(P[r * ld + c], cmul(pcol[r], cmul(prow[c], ip)));
+      else v = csub(P[r * ld + c], cmul(pcol[r], qrow[c]));
       P[r * ld + c] = v;
     }
     __syncthreads();
