@@ -243,6 +243,16 @@ __global__ void k_tc_embed(const double2* __restrict__ W, int N, double scale, i
 // Strain stacks of X (six per vector) and the three displacement components, written as
 // split bf16 K-major columns: E col = s * nvec + vec, X col = vec * 3 + c; K index 2q + {re, im}.
 // Slice t of E sits at E + t * es, of X at X + t * xs.
+// The three bf16 slices of (v.x, v.y) stored as pairs at p, p + ss, p + 2 ss (p 4-byte aligned).
+__device__ __forceinline__ void split3_store2(float2 v, __nv_bfloat16* p, long long ss) {
+  __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+  split3_bf16(v.x, h0, m0, l0);
+  split3_bf16(v.y, h1, m1, l1);
+  *reinterpret_cast<__nv_bfloat162*>(p) = __halves2bfloat162(h0, h1);
+  *reinterpret_cast<__nv_bfloat162*>(p + ss) = __halves2bfloat162(m0, m1);
+  *reinterpret_cast<__nv_bfloat162*>(p + 2 * ss) = __halves2bfloat162(l0, l1);
+}
+
 __global__ void k_tc_split_strain(const float2* __restrict__ X, int nvec, int m, Geom g, const double* __restrict__ Q,
                                   const float4* __restrict__ Kf, int Kp, __nv_bfloat16* __restrict__ E, long long es,
                                   __nv_bfloat16* __restrict__ Xs, long long xs) {
@@ -277,17 +287,10 @@ __global__ void k_tc_split_strain(const float2* __restrict__ X, int nvec, int m,
   e[3] = make_float2((k1 * u2.x + k2 * u1.x) * RS2, (k1 * u2.y + k2 * u1.y) * RS2);
   e[4] = make_float2((k0 * u2.x + k2 * u0.x) * RS2, (k0 * u2.y + k2 * u0.y) * RS2);
   e[5] = make_float2((k0 * u1.x + k1 * u0.x) * RS2, (k0 * u1.y + k1 * u0.y) * RS2);
-  for (int s = 0; s < 6; ++s) {
-    long long o = ((long long)s * nvec + vec) * Kp + 2 * q;
-    split3_bf16(e[s].x, E[o], E[o + es], E[o + 2 * es]);
-    split3_bf16(e[s].y, E[o + 1], E[o + 1 + es], E[o + 1 + 2 * es]);
-  }
+  // (re, im) slices side by side: one 4-byte store per slice (Kp and the slice strides are even)
+  for (int s = 0; s < 6; ++s) split3_store2(e[s], E + ((long long)s * nvec + vec) * Kp + 2 * q, es);
   const float2 uu[3] = {u0, u1, u2};
-  for (int c = 0; c < 3; ++c) {
-    long long o = ((long long)vec * 3 + c) * Kp + 2 * q;
-    split3_bf16(uu[c].x, Xs[o], Xs[o + xs], Xs[o + 2 * xs]);
-    split3_bf16(uu[c].y, Xs[o + 1], Xs[o + 1 + xs], Xs[o + 1 + 2 * xs]);
-  }
+  for (int c = 0; c < 3; ++c) split3_store2(uu[c], Xs + ((long long)vec * 3 + c) * Kp + 2 * q, xs);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
