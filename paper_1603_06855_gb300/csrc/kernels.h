@@ -31,9 +31,12 @@ struct SetupArgs {
   double2* sfac;    // 3 x L^3
   double2* T;       // 3 x N x N   (density, f1, f2), SI
   double2* W;       // 2 x N x N   inverses of the f1, f2 blocks, SI
-  double2* gj_row;  // 2 x 32 x N: old pivot rows of the blocked Gauss-Jordan step
-  double2* gj_col;  // 2 x 32 x (N + 32): pivot-block inverses and column panels
+  double2* gj_row;  // 2 panels x 2 x 32 x N: old pivot rows of the blocked Gauss-Jordan steps
+  double2* gj_col;  // 2 panels x 2 x 32 x (N + 32): pivot-block inverses and column panels
   int* status;
+  cudaStream_t side;       // stream for the next panel's pivot block (or null: one stream)
+  cudaEvent_t ev_rows;     // the next pivot's rows are updated
+  cudaEvent_t ev_pivot;    // the next pivot block is inverted
 };
 int launch_setup(const SetupArgs& a, cudaStream_t s);
 

@@ -95,6 +95,8 @@ struct pc_ctx {
   bool oz_ready = false;         // oz holds the slices of the current design
   cudaStream_t sk[kMaxGroups] = {};  // non-blocking streams of the k groups
   cudaEvent_t ev_fork = nullptr, ev_join[kMaxGroups] = {};
+  cudaEvent_t ev_gj_rows = nullptr, ev_gj_pivot = nullptr;  // look-ahead of the Gauss-Jordan pivot blocks
+  cudaStream_t s_gj = nullptr;  // their stream, at the highest priority: dispatched ahead of the bulk update
   int split = 1;                // PC_SPLIT=0: the block iteration of the mixed form on one stream
   int groups = 2;               // k groups run concurrently (PC_KGROUPS, 2..kMaxGroups)
   std::mutex ph_mu;             // profiling records from the two k-half threads
@@ -271,6 +273,9 @@ extern "C" void pc_destroy(pc_ctx* c) {
     if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_gj_rows) cudaEventDestroy(c->ev_gj_rows);
+  if (c->ev_gj_pivot) cudaEventDestroy(c->ev_gj_pivot);
+  if (c->s_gj) cudaStreamDestroy(c->s_gj);
   delete c;
 }
 
@@ -391,8 +396,8 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
   rc |= dalloc(&c->sfac, 3 * L * L * L);
   rc |= dalloc(&c->T, 3 * NN);
   rc |= dalloc(&c->W, 2 * NN);
-  rc |= dalloc(&c->gj_row, 2 * 32 * (size_t)N);              // blocked Gauss-Jordan: old pivot rows
-  rc |= dalloc(&c->gj_col, 2 * 32 * ((size_t)N + 32));       // pivot-block inverses, column panels
+  rc |= dalloc(&c->gj_row, 4 * 32 * (size_t)N);              // blocked Gauss-Jordan: old pivot rows (2 panels)
+  rc |= dalloc(&c->gj_col, 4 * 32 * ((size_t)N + 32));       // pivot-block inverses, column panels (2 panels)
   rc |= dalloc(&c->status, 1);
   rc |= dalloc(&c->small_flops, 1);
   if (p->precision == PC_MIXED) {
@@ -405,7 +410,15 @@ extern "C" int pc_create(const pc_params* p, pc_ctx** out) {
       cudaEventCreate(&c->ev_s0) != cudaSuccess || cudaEventCreate(&c->ev_s1) != cudaSuccess ||
       cudaEventCreate(&c->ev_g0) != cudaSuccess || cudaEventCreate(&c->ev_g1) != cudaSuccess ||
       cudaMallocHost((void**)&c->h_unconv, kMaxGroups * sizeof(int)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_gj_rows, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_gj_pivot, cudaEventDisableTiming) != cudaSuccess) {
+    pc_destroy(c);
+    return PC_ECUDA;
+  }
+  int prio_low = 0, prio_high = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&c->s_gj, cudaStreamNonBlocking, prio_high) != cudaSuccess) {
     pc_destroy(c);
     return PC_ECUDA;
   }
@@ -522,6 +535,7 @@ extern "C" int pc_set_design(pc_ctx* c, const double* rho, void* stream) {
   a.fields = c->fields; a.dchi = c->dchi; a.chi = c->chi; a.chi_mean = c->chi_mean; a.dfc = c->dfc;
   a.t1 = c->t1; a.t2 = c->t2s; a.sfac = c->sfac; a.T = c->T; a.W = c->W;
   a.gj_row = c->gj_row; a.gj_col = c->gj_col;
+  a.side = c->s_gj; a.ev_rows = c->ev_gj_rows; a.ev_pivot = c->ev_gj_pivot;
   a.status = c->status;
   int rc = launch_setup(a, s);
   if (rc) return rc;

@@ -212,12 +212,15 @@ __global__ void k_gj_colpanel(const double2* __restrict__ A, int N, long long ms
   Cp[(long long)z * GJ_B * N + (long long)i * GJ_B + l] = acc;
 }
 
-// Whole-matrix update of one panel step; one row i per blockIdx.y.
+// Update of one panel step for a set of rows, one row per blockIdx.y: rows r0 + y, except that
+// the nskip rows from skip0 on are stepped over (y >= skip0 - r0 maps to y + nskip).
 __global__ void k_gj_update(double2* __restrict__ A, int N, long long mstride, int k0, int bb,
                             const double2* __restrict__ Pbuf, const double2* __restrict__ Ar,
-                            const double2* __restrict__ Cp) {
+                            const double2* __restrict__ Cp, int r0, int skip0, int nskip) {
   __shared__ double2 crow[GJ_B];
-  const int z = blockIdx.z, i = blockIdx.y;
+  const int z = blockIdx.z;
+  int i = r0 + (int)blockIdx.y;
+  if (i >= skip0) i += nskip;
   const double2* arz = Ar + (long long)z * GJ_B * N;
   const double2* pz = Pbuf + (long long)z * GJ_B * GJ_B;
   const bool iblk = i >= k0 && i < k0 + bb;
@@ -272,14 +275,33 @@ int launch_setup(const SetupArgs& a, cudaStream_t s) {
   // W1 = T_f1^-1, W2 = T_f2^-1
   k_copy2<<<cdiv(2 * NN, 256), 256, 0, s>>>(a.T + NN, a.W, 2 * NN);
   PC_LAUNCH_CHECK();
-  double2* Pbuf = a.gj_col;                          // 2 x GJ_B x GJ_B
-  double2* Cp = a.gj_col + 2LL * GJ_B * GJ_B;       // 2 x N x GJ_B
-  double2* Ar = a.gj_row;                            // 2 x GJ_B x N
-  for (int k0 = 0; k0 < N; k0 += GJ_B) {
-    const int bb = min(GJ_B, N - k0);
-    k_gj_pivot<<<dim3(1, 1, 2), 512, 0, s>>>(a.W, N, NN, k0, bb, Pbuf, Ar);
-    k_gj_colpanel<<<dim3(cdiv((long long)N * bb, 256), 1, 2), 256, 0, s>>>(a.W, N, NN, k0, bb, Pbuf, Cp);
-    k_gj_update<<<dim3(cdiv(N, 256), N, 2), 256, 0, s>>>(a.W, N, NN, k0, bb, Pbuf, Ar, Cp);
+  // Scratch of two panels (parity p): pivot-block inverses, column panels, old pivot rows.
+  const long long colsz = 2LL * GJ_B * (N + GJ_B), rowsz = 2LL * GJ_B * N;
+  double2* Pbuf[2] = {a.gj_col, a.gj_col + colsz};                                   // 2 x GJ_B x GJ_B each
+  double2* Cp[2] = {a.gj_col + 2LL * GJ_B * GJ_B, a.gj_col + colsz + 2LL * GJ_B * GJ_B};  // 2 x N x GJ_B
+  double2* Ar[2] = {a.gj_row, a.gj_row + rowsz};                                     // 2 x GJ_B x N
+  // Look-ahead: the pivot block of panel k + 1 needs only panel k's update of its own rows, so
+  // those rows are updated first and the next pivot block (one CTA per matrix) runs on the side
+  // stream while the main stream updates the other rows.
+  const bool ahead = a.side && a.ev_rows && a.ev_pivot;
+  k_gj_pivot<<<dim3(1, 1, 2), 512, 0, s>>>(a.W, N, NN, 0, min(GJ_B, N), Pbuf[0], Ar[0]);
+  for (int k0 = 0, pi = 0; k0 < N; k0 += GJ_B, ++pi) {
+    const int bb = min(GJ_B, N - k0), p = pi & 1;
+    const int kn = k0 + bb, bbn = min(GJ_B, N - kn);
+    k_gj_colpanel<<<dim3(cdiv((long long)N * bb, 256), 1, 2), 256, 0, s>>>(a.W, N, NN, k0, bb, Pbuf[p], Cp[p]);
+    const dim3 gx(cdiv(N, 256), 1, 2);
+    if (bbn > 0 && ahead) {
+      k_gj_update<<<dim3(gx.x, bbn, 2), 256, 0, s>>>(a.W, N, NN, k0, bb, Pbuf[p], Ar[p], Cp[p], kn, N, 0);
+      PC_CUDA_TRY(cudaEventRecord(a.ev_rows, s));
+      PC_CUDA_TRY(cudaStreamWaitEvent(a.side, a.ev_rows, 0));
+      k_gj_pivot<<<dim3(1, 1, 2), 512, 0, a.side>>>(a.W, N, NN, kn, bbn, Pbuf[p ^ 1], Ar[p ^ 1]);
+      PC_CUDA_TRY(cudaEventRecord(a.ev_pivot, a.side));
+      k_gj_update<<<dim3(gx.x, N - bbn, 2), 256, 0, s>>>(a.W, N, NN, k0, bb, Pbuf[p], Ar[p], Cp[p], 0, kn, bbn);
+      PC_CUDA_TRY(cudaStreamWaitEvent(s, a.ev_pivot, 0));
+    } else {
+      k_gj_update<<<dim3(gx.x, N, 2), 256, 0, s>>>(a.W, N, NN, k0, bb, Pbuf[p], Ar[p], Cp[p], 0, N, 0);
+      if (bbn > 0) k_gj_pivot<<<dim3(1, 1, 2), 512, 0, s>>>(a.W, N, NN, kn, bbn, Pbuf[p ^ 1], Ar[p ^ 1]);
+    }
   }
   PC_LAUNCH_CHECK();
   return PC_OK;
