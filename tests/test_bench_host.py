@@ -1,5 +1,6 @@
 """Host-side pieces of bench.py (CPU): the clock sampler's parsing of nvidia-smi lines, which decides
-which throttle reasons a run reports."""
+which throttle reasons a run reports, and the DRAM-traffic table of the roofline families."""
+import hashlib
 import os
 import sys
 
@@ -47,3 +48,24 @@ def test_no_samples_is_flagged():
     assert _summary([])["reasons"] == ["no samples"]
     cs = bench.ClockSampler(0)
     assert cs.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_traffic_entries_name_existing_sources_and_go_stale_with_them(tmp_path, monkeypatch):
+    """Every roofline family's kernel has a DRAM-traffic entry tied to its source file's SHA-256;
+    a source that differs from the hashed one turns the entry into null instead of a stale number."""
+    for kernel in ("k_tc_gram", "k_tc_update", "k_tc_gemm", "k_small_rr32", "k_oz_gemm", "k_adj_synth12+k_adj_reduce"):
+        t = bench.TRAFFIC[kernel]
+        assert os.path.isfile(os.path.join(ROOT, "paper_1603_06855_gb300", "csrc", t["source"]))
+        assert len(t["sha256"]) == 64 and t["bytes"] > 0
+    assert bench.traffic_per_launch("no_such_kernel") is None
+    # a copy of the tree whose source differs in one byte
+    src = tmp_path / "paper_1603_06855_gb300" / "csrc"
+    src.mkdir(parents=True)
+    entry = bench.TRAFFIC["k_tc_gram"]
+    data = open(os.path.join(ROOT, "paper_1603_06855_gb300", "csrc", entry["source"]), "rb").read()
+    (src / entry["source"]).write_bytes(data)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    same = hashlib.sha256(data).hexdigest() == entry["sha256"]
+    assert bench.traffic_per_launch("k_tc_gram") == (entry["bytes"] if same else None)
+    (src / entry["source"]).write_bytes(data + b" ")
+    assert bench.traffic_per_launch("k_tc_gram") is None
