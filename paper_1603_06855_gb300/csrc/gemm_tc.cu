@@ -47,15 +47,35 @@ __host__ __device__ constexpr uint32_t idesc_bf16() { return idesc_bf16_n(TC_BN)
 // next launch on the same stream.  The stage ring runs on across tiles, and the accumulator
 // alternates between two 128-column halves of tensor memory, so the epilogue warps drain tile i
 // while the MMAs of tile i + 1 run.
-__global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUtensorMap tA_hi,
-                                                    const __grid_constant__ CUtensorMap tA_mid,
-                                                    const __grid_constant__ CUtensorMap tA_lo,
-                                                    const __grid_constant__ CUtensorMap tB_hi,
-                                                    const __grid_constant__ CUtensorMap tB_mid,
-                                                    const __grid_constant__ CUtensorMap tB_lo, int num_kb, int col_base,
-                                                    int ncols, int m_valid, int mtiles, int ntiles,
-                                                    float* __restrict__ C, long long ldc, int* tile_ctr,
-                                                    int* status) {
+// The GEMMs of one launch: up to three segments, each an operator (A maps) times a range of
+// right-hand-side columns (B maps) into its own output; the tiles of segment g are tile0[g] ..
+// tile0[g] + mtiles * ntiles[g] - 1, M-fastest.
+struct TcSeg {
+  int which, bset;         // operator index (A maps), right-hand-side set (B maps)
+  int col_base, ncols;     // columns of the right-hand sides (and of the output)
+  int tile0, ntiles;       // first tile of the segment, column tiles
+  float* C;                // output, column col_base + j at C + (col_base + j) * ldc
+};
+struct TcGemmParams {
+  CUtensorMap A[3][3];     // [operator][slice hi, mid, lo]
+  CUtensorMap B[2][3];     // [right-hand-side set][slice]
+  TcSeg seg[3];
+  int nseg, num_kb, m_valid, mtiles, tiles;
+  long long ldc;
+  int* tile_ctr;
+  int* status;
+};
+__device__ __forceinline__ int tc_segment(const TcGemmParams& P, int t) {
+  int g = 0;
+  while (g + 1 < P.nseg && t >= P.seg[g + 1].tile0) ++g;
+  return g;
+}
+
+__global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ TcGemmParams P) {
+  const int num_kb = P.num_kb, m_valid = P.m_valid, mtiles = P.mtiles;
+  const long long ldc = P.ldc;
+  int* const tile_ctr = P.tile_ctr;
+  int* const status = P.status;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -66,7 +86,7 @@ __global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUte
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + TC_STAGES * STAGE_BYTES + 256);
   volatile int* tile_id = reinterpret_cast<volatile int*>(gbase + TC_STAGES * STAGE_BYTES + 384);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tiles = mtiles * ntiles;
+  const int tiles = P.tiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -106,19 +126,23 @@ __global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUte
         tile_id[slot] = t;
         mbar_arrive(bars + 320 + 8 * slot);
         if (t >= tiles) break;
-        const int m0 = (t % mtiles) * TC_BM, n0 = (t / mtiles) * TC_BN;
+        const TcSeg& sg = P.seg[tc_segment(P, t)];
+        const int lt = t - sg.tile0;
+        const int m0 = (lt % mtiles) * TC_BM, n0 = sg.col_base + (lt / mtiles) * TC_BN;
+        const CUtensorMap* Am = P.A[sg.which];
+        const CUtensorMap* Bm = P.B[sg.bset];
         for (int kb = 0; kb < num_kb; ++kb, ++it) {
           const int s = (int)(it % TC_STAGES);
           const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
           if (!(ok = mbar_wait(bars + 64 + 8 * s, ph ^ 1u, status))) break;
           const uint32_t st = base + s * STAGE_BYTES;
           mbar_expect_tx(bars + 8 * s, STAGE_BYTES);
-          tma_load_2d(st, &tA_hi, bars + 8 * s, kb * TC_BK, m0);
-          tma_load_2d(st + A_TILE, &tA_mid, bars + 8 * s, kb * TC_BK, m0);
-          tma_load_2d(st + 2 * A_TILE, &tA_lo, bars + 8 * s, kb * TC_BK, m0);
-          tma_load_2d(st + 3 * A_TILE, &tB_hi, bars + 8 * s, kb * TC_BK, col_base + n0);
-          tma_load_2d(st + 3 * A_TILE + B_TILE, &tB_mid, bars + 8 * s, kb * TC_BK, col_base + n0);
-          tma_load_2d(st + 3 * A_TILE + 2 * B_TILE, &tB_lo, bars + 8 * s, kb * TC_BK, col_base + n0);
+          tma_load_2d(st, &Am[0], bars + 8 * s, kb * TC_BK, m0);
+          tma_load_2d(st + A_TILE, &Am[1], bars + 8 * s, kb * TC_BK, m0);
+          tma_load_2d(st + 2 * A_TILE, &Am[2], bars + 8 * s, kb * TC_BK, m0);
+          tma_load_2d(st + 3 * A_TILE, &Bm[0], bars + 8 * s, kb * TC_BK, n0);
+          tma_load_2d(st + 3 * A_TILE + B_TILE, &Bm[1], bars + 8 * s, kb * TC_BK, n0);
+          tma_load_2d(st + 3 * A_TILE + 2 * B_TILE, &Bm[2], bars + 8 * s, kb * TC_BK, n0);
         }
       }
     }
@@ -177,8 +201,12 @@ __global__ __launch_bounds__(192, 1) void k_tc_gemm(const __grid_constant__ CUte
       const int b = tl & 1;
       const bool ok = __all_sync(0xffffffffu, mbar_wait(bars + 128 + 8 * b, (uint32_t)(tl >> 1) & 1u, status));
       tc_fence_after();
-      const int row = (t % mtiles) * TC_BM + quad * 32 + lane;
-      const int n0 = (t / mtiles) * TC_BN;
+      const TcSeg& sg = P.seg[tc_segment(P, t)];
+      const int lt = t - sg.tile0;
+      const int row = (lt % mtiles) * TC_BM + quad * 32 + lane;
+      const int n0 = (lt / mtiles) * TC_BN;
+      const int col_base = sg.col_base, ncols = sg.ncols;
+      float* const C = sg.C;
 #pragma unroll 1
       for (int c = 0; c < TC_BN / 16; ++c) {
         float v[16];
@@ -449,8 +477,12 @@ int tc_prepare_operators(TcPlan* p, const double2* W, const double2* T, double w
   return PC_OK;
 }
 
-static int launch_tc_gemm(TcPlan* p, int which_A, const CUtensorMap* b, int col_base, int ncols, float* C,
-                          cudaStream_t s) {
+// One persistent launch over the tiles of up to three GEMM segments.
+struct TcSegSpec {
+  int which, bset, col_base, ncols;
+  float* C;
+};
+static int launch_tc_gemm(TcPlan* p, const TcSegSpec* sp, int nseg, cudaStream_t s) {
   static const int sms = [] {  // queried once; thread-safe static initialisation
     int dev = 0, v = 0;
     cudaGetDevice(&dev);
@@ -458,11 +490,35 @@ static int launch_tc_gemm(TcPlan* p, int which_A, const CUtensorMap* b, int col_
     cudaGetLastError();
     return v;
   }();
-  const int mtiles = p->Mp / TC_BM, ntiles = (ncols + TC_BN - 1) / TC_BN;
-  const int grid = std::min(mtiles * ntiles, sms);
-  k_tc_gemm<<<grid, 192, SMEM_BYTES, s>>>(p->mA_hi[which_A], p->mA_mid[which_A], p->mA_lo[which_A], b[0], b[1], b[2],
-                                          p->Kp / TC_BK, col_base, ncols, 2 * p->N, mtiles, ntiles, C, 2LL * p->N,
-                                          p->tile_ctr, p->status);
+  if (nseg < 1 || nseg > 3) return PC_EINVAL;
+  TcGemmParams P;
+  for (int w = 0; w < 3; ++w) {
+    P.A[w][0] = p->mA_hi[w];
+    P.A[w][1] = p->mA_mid[w];
+    P.A[w][2] = p->mA_lo[w];
+  }
+  for (int t = 0; t < 3; ++t) {
+    P.B[0][t] = p->mE[t];
+    P.B[1][t] = p->mX[t];
+  }
+  const int mtiles = p->Mp / TC_BM;
+  int tiles = 0;
+  for (int g = 0; g < nseg; ++g) {
+    const int nt = (sp[g].ncols + TC_BN - 1) / TC_BN;
+    P.seg[g] = TcSeg{sp[g].which, sp[g].bset, sp[g].col_base, sp[g].ncols, tiles, nt, sp[g].C};
+    tiles += mtiles * nt;
+  }
+  for (int g = nseg; g < 3; ++g) P.seg[g] = TcSeg{0, 0, 0, 0, tiles, 0, nullptr};
+  P.nseg = nseg;
+  P.num_kb = p->Kp / TC_BK;
+  P.m_valid = 2 * p->N;
+  P.mtiles = mtiles;
+  P.tiles = tiles;
+  P.ldc = 2LL * p->N;
+  P.tile_ctr = p->tile_ctr;
+  P.status = p->status;
+  if (tiles == 0) return PC_OK;
+  k_tc_gemm<<<std::min(tiles, sms), 192, SMEM_BYTES, s>>>(P);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
@@ -474,12 +530,12 @@ int tc_apply(TcPlan* p, const float2* X, float2* AX, float2* OX, int nvec, int m
   const long long es = (long long)6 * p->nvec_max * p->Kp, xs = (long long)3 * p->nvec_max * p->Kp;
   k_tc_split_strain<<<cdiv(n, 256), 256, 0, s>>>(X, nvec, m, g, Q, Kf, p->Kp, p->E, es, p->X, xs);
   PC_LAUNCH_CHECK();
-  // E column s * nvec + v holds stack s of vector v (the maps span the plan's capacity).
-  int rc = launch_tc_gemm(p, 0, p->mE, 0, nvec, (float*)p->S, s);
+  // E column s * nvec + v holds stack s of vector v (the maps span the plan's capacity).  One
+  // launch: W1 on the dilatation stack, W2 on the five deviatoric stacks (both into S), T_rho on
+  // the displacements (into OX).
+  const TcSegSpec seg[3] = {{0, 0, 0, nvec, (float*)p->S}, {1, 0, nvec, 5 * nvec, (float*)p->S},
+                            {2, 1, 0, 3 * nvec, (float*)OX}};
+  int rc = launch_tc_gemm(p, seg, 3, s);
   if (rc) return rc;
-  rc = launch_tc_gemm(p, 1, p->mE, nvec, 5 * nvec, (float*)p->S, s);
-  if (rc) return rc;
-  rc = launch_epilogue<float>(p->S, nvec, m, g, Q, 1.0f, 1.0f, AX, s, Kf);
-  if (rc) return rc;
-  return launch_tc_gemm(p, 2, p->mX, 0, 3 * nvec, (float*)OX, s);
+  return launch_epilogue<float>(p->S, nvec, m, g, Q, 1.0f, 1.0f, AX, s, Kf);
 }
