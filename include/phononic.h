@@ -92,7 +92,7 @@ typedef struct {
   double tol;           /* relative residual target of the block iteration (0: default, 1e-8 FP64, 3e-4 mixed).
                            A gradient through one (k, band) pair (a gap) has a relative error of
                            about that pair's final residual: for a 1e-4 gap gradient in the mixed
-                           form pass tol <= 3e-5 (the default suits all-band weighted objectives). */
+                           form pass tol = 1e-4 (the default suits all-band weighted objectives). */
   int max_iter;         /* iteration cap (0: default); hitting it sets PC_ENOCONV */
   int law;              /* PC_LAW_COMPLIANCE (0, default) | PC_LAW_YOUNG; density is linear in chi either way */
 } pc_params;

@@ -230,7 +230,7 @@ def maximize_gap(solver: BandSolver, rho: torch.Tensor, n_lower: int, beta: floa
     heaviside_schedule(step, beta_every) (beta_every = 0: 1 throughout) and the gradient is carried
     back through the map.  Returns the final variables and the gap before each step and after
     the last.  The gradient's relative error is about the final residual of the bands n_lower and
-    n_lower+1: in the mixed form, build the solver with tol <= 3e-5 for a 1e-4 gradient."""
+    n_lower+1: in the mixed form, build the solver with tol = 1e-4 for a 1e-4 gradient."""
     x = rho.detach().to(solver.device, torch.float64).contiguous().clone().view(-1)
     opt = MMA(x.numel(), device=solver.device)
     history = []

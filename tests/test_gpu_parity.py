@@ -252,8 +252,8 @@ def test_largest_projected_problem(B, precision, tol):
     its relative error is about the pair's final residual.  Here the top band is the slowest to
     converge and stops just below the tolerance: at the mixed form's default residual target
     (3e-4) the gap(20,21) gradient is 2.6e-4 from the oracle's, at 1e-4 it is 7.4e-5, at 3e-5
-    1.9e-5.  The mixed case therefore runs at tol = 3e-5, the setting for the 1e-4 gradient
-    bound on objectives through single pairs; the FP64 form runs at its default."""
+    1.9e-5.  The mixed case therefore runs at a tighter tol (3e-5, a margin below the 1e-4
+    that gap objectives need); the FP64 form runs at its default."""
     w = wl.sc16_grf()
     w.nbands = 21
     rng = np.random.default_rng(61)
