@@ -1,8 +1,8 @@
 """The ctypes mirrors of the C ABI (binding.py) match include/phononic.h: a small C program
 compiled against the header prints sizeof and every field's offsetof of the structs and the value
 of every constant, which must equal the ctypes layout and the binding's constants; every entry
-point's ctypes argument and return types agree with its prototype.  CPU only (gcc); a mismatch would make the binding
-read or write the wrong bytes without any error."""
+point's ctypes argument and return types agree with its prototype.  CPU only (gcc); a mismatch
+would make the binding read or write the wrong bytes without any error."""
 import ctypes
 import os
 import shutil
