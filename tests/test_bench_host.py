@@ -1,5 +1,6 @@
 """Host-side pieces of bench.py (CPU): the clock sampler's parsing of nvidia-smi lines, which decides
-which throttle reasons a run reports, and the DRAM-traffic table of the roofline families."""
+which throttle reasons a run reports, the DRAM-traffic table of the roofline families, and the
+reference arm (the oracle timed on the host cores) with its JSON line."""
 import hashlib
 import os
 import sys
@@ -69,3 +70,36 @@ def test_traffic_entries_name_existing_sources_and_go_stale_with_them(tmp_path, 
     assert bench.traffic_per_launch("k_tc_gram") == (entry["bytes"] if same else None)
     (src / entry["source"]).write_bytes(data + b" ")
     assert bench.traffic_per_launch("k_tc_gram") is None
+
+
+def _run_reference_arm(env_extra):
+    import json
+    import subprocess
+    env = dict(os.environ, **env_extra)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_prints_one_line_of_the_contract():
+    """--impl reference times the FP64 oracle on the host cores (one design's assembly and one of
+    its 100 k-points per step, extrapolated) and prints one JSON line with the primary arm's
+    metric, unit and direction, the oracle as cpu_baseline, and an e2e figure with no copies."""
+    lines = _run_reference_arm({"RANK": "0"})
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] == 0 and d["dtype"] == "f64"
+    assert d["value"] > 0 and abs(d["ms_per_step"] - 1000.0 * 100 / d["value"]) <= 1e-6 * d["ms_per_step"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == bench.WORKLOAD
+
+
+def test_reference_arm_is_silent_on_other_ranks():
+    """Under torchrun only rank 0 runs the oracle and prints; the other ranks exit 0 at once."""
+    assert _run_reference_arm({"RANK": "1"}) == []
